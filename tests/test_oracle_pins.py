@@ -1,0 +1,433 @@
+"""Pins of the FP64 oracle against facts fixed by the paper or by mathematics.
+
+None of these compare the oracle with itself: each checks a closed form, an
+invariant, an identity of the discrete scheme, a special case, or a value the
+paper prints.  A plausible mistake in the oracle (a sign, a dropped factor, a
+wrong shift direction, a wrong time pairing, a transposed axis) fails at least
+one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import pstd
+from paper_2102_00755_b300 import synth
+
+os.environ.setdefault("ORACLE_WORKERS", "1")
+
+C_REF = 1800.0
+
+
+def _grid(nx, ny, nz, dx=1e-3, pml=(0, 0, 0)):
+    return pstd.Grid(nx, ny, nz, dx, synth.time_step(dx), C_REF, 1000.0, pml, 2.0)
+
+
+def _kmag_kappa(G):
+    k = [pstd.wavenumbers(n, G.dx) for n in (G.nx, G.ny, G.nz)]
+    kx, ky, kz = k[0][None, None, :], k[1][None, :, None], k[2][:, None, None]
+    km = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
+    a = G.c_ref * G.dt * km / 2.0
+    kap = np.where(a == 0, 1.0, np.sin(a) / np.where(a == 0, 1.0, a))
+    return km, kap
+
+
+# ---------------------------------------------------------------------------
+# k-space derivative, App. B (Eqs. 18-19)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(12, 10, 9), (9, 15, 8)])
+def test_staggered_derivative_of_plane_wave(shape):
+    """d+/dxi cos(k0.x) = -k0_xi kappa(k0) sin(k0.x + k0_xi dx/2), and d- with -dx/2."""
+    nx, ny, nz = shape
+    G = _grid(nx, ny, nz)
+    m0 = (2, -3, 3)
+    k0 = [2 * math.pi * m0[a] / (shape[a] * G.dx) for a in range(3)]
+    X, Y, Z = synth.coords(shape)
+    pos = (X * G.dx, Y * G.dx, Z * G.dx)
+    phase = k0[0] * pos[0] + k0[1] * pos[1] + k0[2] * pos[2]
+    g = np.cos(phase)
+    kap0 = math.sin(G.c_ref * G.dt * math.sqrt(sum(k * k for k in k0)) / 2) / (
+        G.c_ref * G.dt * math.sqrt(sum(k * k for k in k0)) / 2)
+    assert kap0 < 0.97  # the correction is visible at this wavenumber
+    gh = G.fft(g)
+    for a in range(3):
+        dp = G.deriv(gh, G.d_plus[a])
+        dm = G.deriv(gh, G.d_minus[a])
+        exp_p = -k0[a] * kap0 * np.sin(phase + k0[a] * G.dx / 2)
+        exp_m = -k0[a] * kap0 * np.sin(phase - k0[a] * G.dx / 2)
+        scale = abs(k0[a])
+        assert np.abs(dp - exp_p).max() < 1e-10 * scale
+        assert np.abs(dm - exp_m).max() < 1e-10 * scale
+
+
+@pytest.mark.parametrize("shape", [(8, 6, 10), (9, 7, 5), (16, 12, 9)])
+def test_derivative_adjoint_identity(shape):
+    """<D+ a, b> = -<a, D- b> for every axis, even and odd sizes (Nyquist bin kept)."""
+    nx, ny, nz = shape
+    G = _grid(nx, ny, nz)
+    rng = np.random.default_rng(1)
+    a = rng.standard_normal(G.shape)
+    b = rng.standard_normal(G.shape)
+    for ax in range(3):
+        lhs = np.sum(G.deriv(G.fft(a), G.d_plus[ax]) * b)
+        rhs = -np.sum(a * G.deriv(G.fft(b), G.d_minus[ax]))
+        assert abs(lhs - rhs) <= 1e-11 * abs(lhs) + 1e-9
+
+
+def test_derivative_output_is_real_with_nyquist():
+    """The staggered multipliers are Hermitian, so nothing is lost by taking the real part."""
+    G = _grid(8, 6, 4)
+    g = np.random.default_rng(2).standard_normal(G.shape)
+    for ax in range(3):
+        full = np.fft.ifftn(G.d_plus[ax] * np.fft.fftn(g))
+        assert np.abs(full.imag).max() < 1e-12 * np.abs(full.real).max()
+
+
+# ---------------------------------------------------------------------------
+# Homogeneous propagator, closed form per Fourier mode (App. B: exact for a
+# homogeneous medium at c = c_ref)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("c", [1800.0, 1500.0])
+def test_homogeneous_closed_form(c):
+    """Without PML and with uniform c each Fourier mode obeys
+    p_n - 2 cos(th) p_(n-1) + p_(n-2) = c^2 beta (s_n - s_(n-1)) e_src,
+    cos(th) = 1 - 2 (c/c_ref)^2 sin^2(c_ref dt |k| / 2), beta = 2 dt / (dx c),
+    so p_n = sum_m F_m U_(n-m)(cos th) with Chebyshev polynomials U."""
+    G = _grid(10, 12, 9)
+    nt = 40
+    cc = np.full(G.shape, c)
+    src = np.array([3 + 10 * (4 + 12 * 2)])
+    s = synth.ricker(nt, G.dt, 0.3e6)
+    f, _, fields = pstd.forward(G, cc, src, [1.0], s, np.array([0]), record_field=True)
+    km, _ = _kmag_kappa(G)
+    a = G.c_ref * G.dt * km / 2
+    cos_th = 1.0 - 2.0 * (c / G.c_ref) ** 2 * np.sin(a) ** 2
+    e = np.zeros(G.shape)
+    e.reshape(-1)[src] = 1.0
+    e_hat = np.fft.fftn(e)
+    beta = 2.0 * G.dt / (G.dx * c)
+    ds = np.diff(np.concatenate([[0.0], s]))
+    for n in (0, 1, 5, 17, 39):
+        ph = np.zeros(G.shape, dtype=complex)
+        for m in range(n + 1):
+            ph += c * c * beta * ds[m] * e_hat * special.eval_chebyu(n - m, cos_th)
+        p_exact = np.real(np.fft.ifftn(ph))
+        ref = np.abs(fields[n]).max()
+        assert ref > 0
+        assert np.abs(fields[n] - p_exact).max() < 1e-11 * ref, n
+
+
+# ---------------------------------------------------------------------------
+# Point-source Green's function (physical scale of the source conversion, App. B)
+# ---------------------------------------------------------------------------
+def test_point_source_greens_function():
+    """A point pressure source s converted to a mass source by 2 dt / (3 dx c0)
+    per split component is a monopole of mass rate 2 dx^2 s / c0, so in free
+    space p(r, t) = dx^2 s'(t - r/c) / (2 pi c r); p_n sits at t_n + dt/2."""
+    n, dx, c, f0, nt = 48, 1e-3, 1500.0, 0.15e6, 170
+    G = _grid(n, n, n, dx)
+    cc = np.full(G.shape, c)
+    ctr = n // 2
+    src = np.array([ctr + n * (ctr + n * ctr)])
+    offs = [(6, 0, 0), (0, 0, -6), (4, 4, 3)]
+    recs = np.array([(ctr + o[0]) + n * ((ctr + o[1]) + n * (ctr + o[2])) for o in offs])
+    s = synth.ricker(nt, G.dt, f0)
+    f, _ = pstd.forward(G, cc, src, [1.0], s, recs)
+    t = np.arange(nt) * G.dt + G.dt / 2
+    t0 = 1.5 / f0
+    for k, o in enumerate(offs):
+        r = math.sqrt(sum(x * x for x in o)) * dx
+        tau = t - r / c - t0
+        ap = 2 * math.pi ** 2 * f0 ** 2 * tau
+        a = (math.pi * f0 * tau) ** 2
+        sdot = (-2 * ap - (1 - 2 * a) * ap) * np.exp(-a)
+        an = dx ** 2 * sdot / (2 * math.pi * c * r)
+        rel = np.linalg.norm(f[:, k] - an) / np.linalg.norm(an)
+        amp = np.dot(f[:, k], an) / np.dot(an, an)
+        assert rel < 0.04, (k, rel)
+        assert abs(amp - 1.0) < 0.03, (k, amp)
+
+
+# ---------------------------------------------------------------------------
+# Energy invariant of the leapfrog scheme (PML off) and PML absorption
+# ---------------------------------------------------------------------------
+def _apply_L(G, p):
+    """L p = sum_xi D-_xi D+_xi p = F^-1{ -kappa^2 |k|^2 F p } (closed form of the product)."""
+    km, kap = _kmag_kappa(G)
+    return np.real(np.fft.ifftn(-(kap ** 2) * km ** 2 * np.fft.fftn(p)))
+
+
+def test_energy_conserved_without_pml():
+    """E_(n+1/2) = sum (p_(n+1) - p_n)^2 / c^2 - dt^2 sum p_(n+1) L p_n is exactly
+    conserved once the source is silent (heterogeneous c, W = diag(1/c^2))."""
+    G = _grid(12, 10, 11)
+    rng = np.random.default_rng(3)
+    c = 1500.0 + 200.0 * rng.random(G.shape)
+    nt = 60
+    s = np.zeros(nt)
+    s[:12] = synth.ricker(12, G.dt, 0.4e6, t0=6 * G.dt)
+    src = np.array([5 + 12 * (5 + 10 * 5)])
+    _, _, fields = pstd.forward(G, c, src, [1.0], s, np.array([0]), record_field=True)
+    E = []
+    for n in range(14, nt - 1):
+        d = fields[n + 1] - fields[n]
+        E.append(np.sum(d * d / c ** 2) - G.dt ** 2 * np.sum(fields[n + 1] * _apply_L(G, fields[n])))
+    E = np.array(E)
+    assert E[0] > 0
+    assert np.abs(E - E[0]).max() < 1e-11 * E[0]
+
+
+def test_pml_profile_properties():
+    """Lambda = 1 in the interior, in (0, 1) inside the layer, decreasing towards the edge."""
+    n, P = 30, 8
+    for stag in (False, True):
+        lam = pstd.pml_profile(n, P, 2.0, C_REF, 1e-3, synth.time_step(1e-3), stag)
+        assert np.all(lam[P:n - 1 - P] == 1.0)
+        assert np.all((lam > 0) & (lam <= 1))
+        assert np.all(np.diff(lam[:P + 1]) >= 0) and np.all(np.diff(lam[n - 1 - P:]) <= 0)
+        assert lam[0] < 0.9 and lam[-1] < 0.9
+
+
+def test_pml_absorbs():
+    """With the PML on, the field energy left after the pulse has crossed the
+    domain is a small fraction of its peak; without it, nothing leaves."""
+    out = {}
+    for P in (0, 8):
+        G = _grid(32, 32, 32, pml=(P, P, P))
+        c = np.full(G.shape, 1500.0)
+        nt = 150
+        s = synth.ricker(nt, G.dt, 0.3e6)
+        src = np.array([16 + 32 * (16 + 32 * 16)])
+        _, _, fields = pstd.forward(G, c, src, [1.0], s, np.array([0]), record_field=True)
+        e = np.array([np.sum(fields[n] ** 2) for n in range(nt)])
+        out[P] = e[-1] / e.max()
+    assert out[8] < 0.02 and out[0] > 0.2
+
+
+# ---------------------------------------------------------------------------
+# Reciprocity (symmetric W and L): trace(B <- A) c_A = trace(A <- B) c_B
+# ---------------------------------------------------------------------------
+def test_reciprocity_heterogeneous():
+    G = _grid(12, 11, 10)
+    rng = np.random.default_rng(4)
+    c = 1450.0 + 300.0 * rng.random(G.shape)
+    nt = 50
+    s = synth.ricker(nt, G.dt, 0.35e6)
+    A = 2 + 12 * (3 + 11 * 2)
+    B = 9 + 12 * (7 + 11 * 6)
+    fa, _ = pstd.forward(G, c, np.array([A]), [1.0], s, np.array([B]))
+    fb, _ = pstd.forward(G, c, np.array([B]), [1.0], s, np.array([A]))
+    cA, cB = c.reshape(-1)[A], c.reshape(-1)[B]
+    assert abs(cA - cB) > 10
+    lhs, rhs = fa[:, 0] * cA, fb[:, 0] * cB
+    assert np.abs(lhs - rhs).max() < 1e-10 * np.abs(lhs).max()
+
+
+# ---------------------------------------------------------------------------
+# Gradient: finite differences (exact pairing, no PML, layer = Gamma)
+# ---------------------------------------------------------------------------
+def _smooth_direction(wl, rng):
+    X, Y, Z = synth.coords((wl.nx, wl.ny, wl.nz))
+    d = np.zeros(wl.shape)
+    for _ in range(3):
+        kx, ky, kz = rng.integers(0, 3, size=3)
+        ph = rng.uniform(0, 2 * math.pi, size=3)
+        d += np.cos(2 * math.pi * kx * X / wl.nx + ph[0]) * np.cos(2 * math.pi * ky * Y / wl.ny + ph[1]) \
+            * np.cos(2 * math.pi * kz * Z / wl.nz + ph[2])
+    m = np.zeros(wl.n_vox)
+    m[wl.gamma_idx] = 1.0
+    d *= m.reshape(wl.shape)
+    return d / np.abs(d).max()
+
+
+def _misfit(G, wl, c, f_obs):
+    f, _ = pstd.forward(G, c, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx)
+    return pstd.adjoint_source(f, f_obs)[0]
+
+
+def test_gradient_matches_finite_differences_exact_pairing():
+    """<grad D, delta> equals the central difference of D along smooth directions
+    supported in Gamma; transducers sit in water (c = c_rec) outside Gamma."""
+    wl = synth.small_workload(14, 13, 12, 70, pml=0, layer=6, n_src=2, n_rec=20, K=1, f0=0.3e6)
+    G = pstd.grid_for(wl, pml_on=False)
+    gam = np.zeros(wl.n_vox, bool)
+    gam[wl.gamma_idx] = True
+    assert not gam[wl.src_idx].any() and not gam[wl.rec_idx].any()
+    assert len(wl.layer_idx) == len(wl.gamma_idx)            # layer covers Gamma
+    assert np.all(wl.c_model.reshape(-1)[wl.rec_idx] == wl.c_rec)
+    f_obs, _ = pstd.forward(G, wl.c_true, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx)
+    _, D, grad = pstd.fwi_gradient(G, wl.c_model, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx,
+                                   wl.layer_idx, wl.gamma_idx, f_obs, pairing="exact", c_rec=wl.c_rec)
+    rng = np.random.default_rng(11)
+    h = 1e-2
+    for _ in range(3):
+        d = _smooth_direction(wl, rng)
+        fd = (_misfit(G, wl, wl.c_model + h * d, f_obs) - _misfit(G, wl, wl.c_model - h * d, f_obs)) / (2 * h)
+        an = float(np.sum(grad * d))
+        assert abs(fd) > 0
+        assert abs(an - fd) < 1e-6 * abs(fd), (an, fd)
+
+
+def test_literal_pairing_converges_to_exact():
+    """Alg. 1 as printed pairs the adjoint one step later than the exact discrete
+    adjoint; the two gradients agree to O(dt): halving dt halves their distance."""
+    rel = []
+    for refine in (1, 2):
+        dx = 1e-3
+        dt = synth.time_step(dx) / refine
+        nt = 50 * refine
+        wl = synth.small_workload(12, 12, 10, nt, pml=0, layer=6, n_src=1, n_rec=16, K=1, f0=0.25e6)
+        wl.dt = dt
+        wl.wavelet = synth.ricker(nt, dt, 0.25e6)
+        G = pstd.grid_for(wl, pml_on=False)
+        f_obs, _ = pstd.forward(G, wl.c_true, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx)
+        out = {}
+        for pairing in ("literal", "exact"):
+            out[pairing] = pstd.fwi_gradient(G, wl.c_model, wl.src_idx, wl.weights[0], wl.wavelet,
+                                             wl.rec_idx, wl.layer_idx, wl.gamma_idx, f_obs,
+                                             pairing=pairing, c_rec=wl.c_rec)[2]
+        rel.append(np.linalg.norm(out["literal"] - out["exact"]) / np.linalg.norm(out["exact"]))
+    assert rel[0] < 0.5
+    assert 1.6 < rel[0] / rel[1] < 2.6, rel
+
+
+# ---------------------------------------------------------------------------
+# Time reversal (Sec. 3.1, Sec. 4.3 / Table 2)
+# ---------------------------------------------------------------------------
+def test_tr_equals_stored_field_when_layer_covers_gamma():
+    wl = synth.small_workload(14, 12, 12, 60, pml=3, layer=6, n_src=2, n_rec=20, K=1)
+    assert len(wl.layer_idx) == len(wl.gamma_idx)
+    G = pstd.grid_for(wl)
+    f_obs, _ = pstd.forward(G, wl.c_true, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx)
+    args = (G, wl.c_model, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx, wl.layer_idx,
+            wl.gamma_idx, f_obs)
+    for pairing in ("literal", "exact"):
+        _, D1, g_tr = pstd.fwi_gradient(*args, pairing=pairing)
+        _, D2, g_full = pstd.fwi_gradient(*args, pairing=pairing, full=True)
+        assert D1 == D2
+        assert np.abs(g_tr - g_full).max() < 1e-12 * np.abs(g_full).max()
+
+
+def test_tr_error_decreases_with_layer_thickness():
+    """Like Table 2: the TR gradient approaches the stored-field gradient as the layer thickens."""
+    errs = []
+    for L in (1, 2):
+        wl = synth.small_workload(22, 22, 20, 90, pml=3, layer=L, n_src=2, n_rec=24, K=1, seed=5,
+                                  gamma_frac=0.3)
+        assert len(wl.layer_idx) < len(wl.gamma_idx)
+        G = pstd.grid_for(wl)
+        f_obs, _ = pstd.forward(G, wl.c_true, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx)
+        args = (G, wl.c_model, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx, wl.layer_idx,
+                wl.gamma_idx, f_obs)
+        g_tr = pstd.fwi_gradient(*args)[2]
+        g_full = pstd.fwi_gradient(*args, full=True)[2]
+        errs.append(np.linalg.norm(g_tr - g_full) / np.linalg.norm(g_full))
+    assert errs[1] < 0.5 * errs[0], errs
+
+
+# ---------------------------------------------------------------------------
+# Source encoding (Sec. 3.2, App. E)
+# ---------------------------------------------------------------------------
+def test_encoded_forward_is_linear():
+    wl = synth.small_workload(12, 10, 10, 40, pml=3, n_src=3, n_rec=12, K=1)
+    G = pstd.grid_for(wl)
+    w = np.array([1.0, -1.0, 1.0])
+    f_enc, g_enc = pstd.forward(G, wl.c_model, wl.src_idx, w, wl.wavelet, wl.rec_idx, wl.layer_idx)
+    f_sum = 0
+    g_sum = 0
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = 1.0
+        fi, gi = pstd.forward(G, wl.c_model, wl.src_idx, e, wl.wavelet, wl.rec_idx, wl.layer_idx)
+        f_sum = f_sum + w[i] * fi
+        g_sum = g_sum + w[i] * gi
+    assert np.abs(f_enc - f_sum).max() < 1e-12 * np.abs(f_enc).max()
+    assert np.abs(g_enc - g_sum).max() < 1e-12 * np.abs(g_enc).max()
+
+
+def test_encoding_unbiased_over_all_sign_patterns():
+    """E[w_i w_j] = delta_ij: the mean of the encoded gradient over all 2^3 Rademacher
+    patterns equals the sum of the single-source gradients (App. E)."""
+    wl = synth.small_workload(12, 11, 10, 40, pml=3, n_src=3, n_rec=14, K=1, layer=1)
+    G = pstd.grid_for(wl)
+    f_i = []
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = 1.0
+        f_i.append(pstd.forward(G, wl.c_true, wl.src_idx, e, wl.wavelet, wl.rec_idx)[0])
+    f_i = np.stack(f_i)
+
+    def grad_for(w):
+        f_obs = pstd.encode_data(w, f_i)
+        return pstd.fwi_gradient(G, wl.c_model, wl.src_idx, w, wl.wavelet, wl.rec_idx,
+                                 wl.layer_idx, wl.gamma_idx, f_obs)
+
+    total = 0
+    for i in range(3):
+        e = np.zeros(3)
+        e[i] = 1.0
+        total = total + grad_for(e)[2]
+    mean = 0
+    Dmean = 0
+    for bits in range(8):
+        w = np.array([1.0 if (bits >> i) & 1 else -1.0 for i in range(3)])
+        _, D, g = grad_for(w)
+        mean = mean + g / 8
+        Dmean += D / 8
+    assert np.abs(mean - total).max() < 1e-10 * np.abs(total).max()
+    Dsum = sum(grad_for(np.eye(3)[i])[1] for i in range(3))
+    assert abs(Dmean - Dsum) < 1e-10 * Dsum
+
+
+def test_adjoint_source_definitions():
+    """q^n = f^(Nt-n) - f_obs^(Nt-n), D = 0.5 sum q^2, Q^n = sum_(m<=n) q^m (Alg. 1)."""
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((7, 3))
+    fo = rng.standard_normal((7, 3))
+    D, Q = pstd.adjoint_source(f, fo)
+    Nt = 6
+    acc = np.zeros(3)
+    tot = 0.0
+    for n in range(7):
+        q = f[Nt - n] - fo[Nt - n]
+        tot += 0.5 * float(q @ q)
+        acc = acc + q
+        assert np.allclose(Q[n], acc, rtol=0, atol=1e-14)
+    assert abs(D - tot) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Values the paper prints (tests/golden/paper_setup.txt)
+# ---------------------------------------------------------------------------
+def _golden():
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_setup.txt")
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_paper_time_step():
+    g = _golden()
+    dt = synth.time_step(g["dx_m"], g["c_max"], g["cfl"])
+    assert round(dt * 1e9, 1) == g["dt_ns"]
+
+
+def test_paper_grid_and_pml_rule():
+    """221 x 221 x 111 mm at 0.5 mm is 442 x 442 x 222 voxels (Sec. 4.1); the App. B
+    PML rule (10..20 cells, smallest largest prime factor) pads it to FFT-friendly sizes."""
+    g = _golden()
+    n = [int(round(g[k] / g["dx_mm"])) for k in ("domain_x_mm", "domain_y_mm", "domain_z_mm")]
+    assert n == [int(g["nx"]), int(g["ny"]), int(g["nz"])]
+    for m in n:
+        P = synth.optimal_pml(m)
+        assert 10 <= P <= 20
+        tot = m + 2 * P
+        for p in (7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47):
+            assert tot % p != 0
