@@ -1,0 +1,159 @@
+/*
+ * fwi.h -- C ABI of the B300 time-domain FWI hot path.
+ *
+ * The library computes, for a 3D sound-speed model c0 on a regular grid, the
+ * paper's time-reversal based misfit gradient (Alg. 1, App. B): a forward
+ * k-space pseudospectral simulation of the lossless split-density acoustic
+ * system (first-order system of Sec. 2.1 with the k-space derivative of
+ * Eqs. 18-19 and PML multipliers), a time-reversed re-simulation of the forward
+ * field driven by its trace on a boundary layer of Gamma (Eq. 11, Sec. 3.1),
+ * and an adjoint simulation driven by the time-integrated residual; the product
+ * 2/(dt c0^3) (p+ - 2 p0 + p-) p_adj is accumulated in FP64 over time on Gamma
+ * (discrete form of Eq. 10).  Sources are encoded super-shots
+ * s_hat = sum_i w_i s_i (Sec. 3.2).
+ *
+ * Conventions shared by every call
+ *   - Grid arrays are linear in i + nx*(j + ny*k) (x fastest), FP32 unless noted.
+ *   - "device" pointers are CUDA global-memory pointers owned by the caller;
+ *     "host" pointers are ordinary CPU memory read during the call only.
+ *   - Calls that take a stream are asynchronous on that stream (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream).  Their outputs are valid
+ *     once the stream has reached them.  A plan must not be used from two
+ *     host threads or on two streams at once; distinct plans are independent.
+ *   - Errors are returned as fwi_status; nothing is thrown across the ABI.
+ *     Argument and index validation is done on the host at plan creation and
+ *     at each call.  The sound speed is range-checked on the device
+ *     (0 < c0 <= c_ref, the stability condition of App. B); a violation makes
+ *     the call's kernels skip their work and is reported by fwi_plan_status().
+ *   - No device memory is allocated after fwi_plan_bind_workspace(): every
+ *     buffer lives in the caller-provided workspace.
+ */
+#ifndef FWI_H
+#define FWI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fwi_status {
+  FWI_OK = 0,
+  FWI_EINVAL = 1,       /* bad argument, size or index list                        */
+  FWI_ENOMEM = 2,       /* workspace too small / host allocation failed            */
+  FWI_EUNSTABLE = 3,    /* c0 outside (0, c_ref]: scheme unstable (App. B)         */
+  FWI_ETIMEOUT = 4,     /* a bounded device wait gave up                           */
+  FWI_ECUDA = 5,        /* a CUDA runtime call failed                              */
+  FWI_ECANCELLED = 6,   /* work was cancelled before it ran                        */
+  FWI_ENOTSUP = 7       /* grid shape not supported by this build                  */
+} fwi_status;
+
+typedef enum fwi_pairing {
+  /* Alg. 1 as printed: adjoint steps n = 1..Nt-1 inject the cumulative residual
+   * Q^n and are paired with the TR second difference centred at t_(Nt-n).      */
+  FWI_PAIRING_LITERAL = 0,
+  /* exact discrete adjoint of the PML-free scheme: adjoint steps j = 0..Nt
+   * inject Q^j and are paired with p_(Nt-j) - 2 p_(Nt-j-1) + p_(Nt-j-2).      */
+  FWI_PAIRING_EXACT = 1
+} fwi_pairing;
+
+/* Problem description (host memory, copied by fwi_plan_create). */
+typedef struct fwi_problem {
+  int32_t nx, ny, nz;       /* FFT grid including the PML; each a product of 2, 3, 5  */
+  int32_t pml[3];           /* PML thickness per axis in cells, inside the grid       */
+  double dx;                /* grid spacing [m]                                       */
+  double dt;                /* time step [s]; stability needs c0 <= c_ref             */
+  double c_ref;             /* reference speed of the kappa correction (Eq. 18)       */
+  double rho0;              /* constant ambient density [kg/m^3]                      */
+  double pml_alpha;         /* PML strength: sigma = alpha c_ref/dx (d/P)^4           */
+  double c_rec;             /* >0: gradient returned as dD/dc (raw accumulator times
+                               dx*c_rec/2, exact when every receiver sits in c_rec);
+                               0: the raw Alg. 1 accumulator                          */
+  int32_t nt;               /* time samples = forward iterations (Nt + 1)             */
+  int32_t n_src;            /* emitters                                               */
+  int32_t n_rec;            /* receivers (measurement channels, operator M)           */
+  int32_t n_layer;          /* voxels of the TR boundary layer (subset of Gamma)      */
+  int32_t n_gamma;          /* voxels of the reconstruction region Gamma              */
+  const int32_t *src_idx;   /* host [n_src] linear voxel index of each emitter        */
+  const int32_t *rec_idx;   /* host [n_rec] linear voxel index of each receiver       */
+  const int32_t *layer_idx; /* host [n_layer] strictly increasing, each in gamma_idx  */
+  const int32_t *gamma_idx; /* host [n_gamma] strictly increasing                     */
+  const float *wavelet;     /* host [nt] emitted pressure signal s(t_n)               */
+  int32_t pairing;          /* fwi_pairing                                            */
+  int32_t max_shots;        /* largest K (super-shots per call) this plan serves      */
+} fwi_problem;
+
+typedef struct fwi_plan fwi_plan;
+
+/*
+ * Validate `prob`, build the host-side tables (wavenumbers, kappa inputs,
+ * staggering shifts, PML profiles, FFT radix schedules, per-plane sparse lists)
+ * and report the device workspace size needed.  No device memory is touched.
+ *   workspace_bytes: out, bytes the caller must provide to fwi_plan_bind_workspace.
+ *   out: out, the new plan (free with fwi_plan_destroy).
+ * Errors: FWI_EINVAL (bad sizes/indices, duplicate or unsorted gamma/layer, layer
+ * voxel outside gamma, nt < 3), FWI_ENOTSUP (a dimension with a prime factor
+ * other than 2, 3, 5, or a plane too large for shared memory), FWI_ENOMEM.
+ */
+fwi_status fwi_plan_create(const fwi_problem *prob, size_t *workspace_bytes, fwi_plan **out);
+
+/*
+ * Give the plan its device workspace (>= the reported size, 256-byte aligned)
+ * and upload the constant tables (synchronous).  The memory stays owned by the
+ * caller and must outlive every call made with the plan.
+ * Errors: FWI_EINVAL (NULL or misaligned), FWI_ENOMEM (too small), FWI_ECUDA.
+ */
+fwi_status fwi_plan_bind_workspace(fwi_plan *plan, void *dev_ptr, size_t bytes);
+
+/*
+ * Forward simulations of K encoded super-shots (Alg. 1, forward loop).
+ *   c:       device [nx*ny*nz] sound speed c0 [m/s]
+ *   weights: device [K][n_src] encoding weights w (Sec. 3.2), e.g. Rademacher +-1
+ *   traces:  device out [K][nt][n_rec], f^n = M p after iteration n
+ * Errors: FWI_EINVAL (K outside 1..max_shots, NULL pointer), FWI_ECUDA.
+ */
+fwi_status fwi_forward(fwi_plan *plan, const float *c, const float *weights, int32_t K,
+                       float *traces, void *stream);
+
+/*
+ * Misfit and sound-speed gradient, averaged over K encoded super-shots
+ * (Alg. 1 whole; mean of independent estimates, Sec. 4.5).
+ *   c:        device [N] sound speed
+ *   weights:  device [K][n_src]
+ *   observed: device observed data; observed_encoded = 1: [K][nt][n_rec], already
+ *             encoded as f_hat = sum_i w_i f_i; observed_encoded = 0: raw per-source
+ *             data [n_src][nt][n_rec], encoded on the device with `weights`.
+ *   misfit:   device out [K] FP64, D_k = 0.5 ||q_k||^2
+ *   grad:     device out [N] FP64, (1/K) sum_k of the gradient on Gamma, 0 elsewhere
+ *   traces:   device out [K][nt][n_rec] simulated traces, or NULL
+ * Errors: FWI_EINVAL, FWI_ECUDA.
+ */
+fwi_status fwi_gradient(fwi_plan *plan, const float *c, const float *weights, int32_t K,
+                        const float *observed, int32_t observed_encoded, double *misfit,
+                        double *grad, float *traces, void *stream);
+
+/*
+ * Wait for the plan's last call and report its device-side status:
+ * FWI_EUNSTABLE if its sound speed was outside (0, c_ref] (the call's outputs are
+ * then undefined), FWI_ECUDA on an asynchronous CUDA error, else FWI_OK.
+ */
+fwi_status fwi_plan_status(fwi_plan *plan);
+
+/* Voxel-steps one call performs: (forward + TR + adjoint iterations) * voxels * K. */
+int64_t fwi_plan_voxel_steps(const fwi_plan *plan, int32_t K, int32_t gradient);
+
+/* Number of kernel launches one call issues (for launch accounting). */
+int64_t fwi_plan_launches(const fwi_plan *plan, int32_t K, int32_t gradient);
+
+/* Release the plan's host memory (not the workspace, which the caller owns). */
+fwi_status fwi_plan_destroy(fwi_plan *plan);
+
+/* Static description of a status code. */
+const char *fwi_status_string(fwi_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FWI_H */

@@ -1,0 +1,748 @@
+// C ABI of the B300 time-domain FWI hot path: plan, workspace, forward and
+// gradient calls (Alg. 1, App. B).  See include/fwi.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/fwi.h"
+#include "kernels.cuh"
+
+using namespace fwi;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------ small kernels
+__global__ void k_prepare_c(const float* __restrict__ c, float* __restrict__ c2, int64_t n,
+                            float c_ref, int* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = c[i];
+    if (!(v > 0.f && v <= c_ref)) *bad = 1;
+    c2[i] = v * v;
+  }
+}
+
+// per-call coefficients at the sparse voxels (FP64 arithmetic, FP32 result)
+__global__ void k_prepare_coefs(const float* __restrict__ c, double dt, double dx,
+                                const int* us_vox, int n_us, float* us_coef,
+                                const int* ur_vox, int n_ur, float* ur_coef,
+                                const int* gam_idx, int n_gamma, float* coefG,
+                                const int* lay_idx, int n_layer, float* inv3c2) {
+  const int tot = n_us + n_ur + n_gamma + n_layer;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += gridDim.x * blockDim.x) {
+    if (i < n_us) {
+      us_coef[i] = (float)(2.0 * dt / (3.0 * dx * (double)c[us_vox[i]]));
+    } else if (i < n_us + n_ur) {
+      const int u = i - n_us;
+      ur_coef[u] = (float)(2.0 * dt / (3.0 * dx * (double)c[ur_vox[u]]));
+    } else if (i < n_us + n_ur + n_gamma) {
+      const int j = i - n_us - n_ur;
+      const double cv = c[gam_idx[j]];
+      coefG[j] = (float)(2.0 / (dt * cv * cv * cv));
+    } else {
+      const int j = i - n_us - n_ur - n_gamma;
+      const double cv = c[lay_idx[j]];
+      inv3c2[j] = (float)(1.0 / (3.0 * cv * cv));
+    }
+  }
+}
+
+// amp[k][n][u] = coef_u * (sum_{i at u} w[k][i]) * s(t_n): the encoded source (Sec. 3.2)
+__global__ void k_source_amp(const float* __restrict__ w, int n_src, const float* __restrict__ coef,
+                             const int* mptr, const int* mem, int n_us, const float* __restrict__ wav,
+                             int nt, float* __restrict__ amp) {
+  const int n = blockIdx.x;
+  const int k = blockIdx.y;
+  const float s = wav[n];
+  for (int u = threadIdx.x; u < n_us; u += blockDim.x) {
+    float ws = 0.f;
+    for (int e = mptr[u]; e < mptr[u + 1]; ++e) ws += w[(size_t)k * n_src + mem[e]];
+    amp[((size_t)k * nt + n) * n_us + u] = coef[u] * ws * s;
+  }
+}
+
+// f_hat[k][n][r] = sum_i w[k][i] f_i[n][r] (Sec. 3.2), FP64 accumulation
+__global__ void k_encode(const float* __restrict__ raw, const float* __restrict__ w, int n_src,
+                         int K, int64_t per_src, float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per_src;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc[kMaxSims];
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (int i = 0; i < n_src; ++i) {
+      const double v = raw[(size_t)i * per_src + e];
+      for (int k = 0; k < K; ++k) acc[k] += (double)w[(size_t)k * n_src + i] * v;
+    }
+    for (int k = 0; k < K; ++k) out[(size_t)k * per_src + e] = (float)acc[k];
+  }
+}
+
+// q^n = f^(Nt-n) - f_obs^(Nt-n); Q^n = sum_{m<=n} q^m (FP64 running sum, FP32 store);
+// block partials of D = 0.5 sum q^2 (Alg. 1)
+__global__ void k_misfit(const float* __restrict__ f, const float* __restrict__ fo, int nt, int n_rec,
+                         float* __restrict__ qf, double* __restrict__ dpart) {
+  const int k = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  double d = 0.0;
+  if (r < n_rec) {
+    const float* fk = f + (size_t)k * nt * n_rec;
+    const float* ok = fo + (size_t)k * nt * n_rec;
+    float* qk = qf + (size_t)k * nt * n_rec;
+    double acc = 0.0;
+    for (int n = 0; n < nt; ++n) {
+      const size_t src = (size_t)(nt - 1 - n) * n_rec + r;
+      const double q = (double)fk[src] - (double)ok[src];
+      acc += q;
+      d += 0.5 * q * q;
+      qk[(size_t)n * n_rec + r] = (float)acc;
+    }
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = d;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dpart[(size_t)k * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void k_misfit_final(const double* dpart, int nblk, int K, double* misfit) {
+  const int k = threadIdx.x;
+  if (k < K) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += dpart[(size_t)k * nblk + b];
+    misfit[k] = s;
+  }
+}
+
+// grad_k(Gamma) += 2/(dt c0^3) (p+ - 2 p0 + p-) p_adj  (FP64 accumulator, Alg. 1)
+__global__ void k_accumulate(const float* __restrict__ ring, const float* __restrict__ pa,
+                             const float* __restrict__ coefG, int n_gamma, int sa, int sb, int sc,
+                             double* __restrict__ acc, const int* bad) {
+  if (*bad) return;
+  const int k = blockIdx.y;
+  const float* rk = ring + (size_t)k * 3 * n_gamma;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_gamma; j += gridDim.x * blockDim.x) {
+    const float d2 = rk[(size_t)sa * n_gamma + j] - 2.f * rk[(size_t)sb * n_gamma + j] +
+                     rk[(size_t)sc * n_gamma + j];
+    acc[(size_t)k * n_gamma + j] += (double)(coefG[j] * d2 * pa[(size_t)k * n_gamma + j]);
+  }
+}
+
+__global__ void k_grad_final(const double* __restrict__ acc, const int* __restrict__ gam_idx,
+                             int n_gamma, int K, double scale, double* __restrict__ grad) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_gamma; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s += acc[(size_t)k * n_gamma + j];
+    grad[gam_idx[j]] = scale * s / K;
+  }
+}
+
+// ------------------------------------------------------------ host helpers
+bool factor235(int n, AxisPlan* A) {
+  int m = n, ns = 0;
+  while (m % 8 == 0) { A->radix[ns++] = 8; m /= 8; }
+  while (m % 4 == 0) { A->radix[ns++] = 4; m /= 4; }
+  while (m % 2 == 0) { A->radix[ns++] = 2; m /= 2; }
+  while (m % 3 == 0) { A->radix[ns++] = 3; m /= 3; }
+  while (m % 5 == 0) { A->radix[ns++] = 5; m /= 5; }
+  if (m != 1 || ns > kMaxStages) return false;
+  A->n = n;
+  A->nstages = ns;
+  return true;
+}
+
+double wavenumber(int j, int n, double dx) {
+  const int m = (j < (n + 1) / 2) ? j : j - n;
+  return 2.0 * kPi * m / (n * dx);
+}
+
+// PML multiplier (reading of App. B): sigma = alpha c_ref/dx (d/P)^4, Lambda = exp(-sigma dt/2)
+double pml_value(int i, int n, int P, double alpha, double c_ref, double dx, double dt, bool stag) {
+  if (P <= 0 || alpha == 0.0) return 1.0;
+  const double x = i + (stag ? 0.5 : 0.0);
+  double d = 0.0;
+  if (x < P) d = P - x;
+  else if (x > n - 1 - P) d = x - (n - 1 - P);
+  const double sigma = alpha * (c_ref / dx) * std::pow(d / P, 4.0);
+  return std::exp(-sigma * dt / 2.0);
+}
+
+struct Csr {
+  std::vector<int> ptr;   // [nz+1]
+  std::vector<int> off;   // plane offset of each entry
+  std::vector<int> vox;   // linear voxel of each entry
+  std::vector<int> mptr;  // members per entry
+  std::vector<int> mem;   // member ids
+};
+
+// unique voxels sorted by (z, offset), with the list of ids mapping to each
+Csr build_unique(const int32_t* idx, int n, int nz, int plane) {
+  std::map<int, std::vector<int>> by;
+  for (int i = 0; i < n; ++i) by[idx[i]].push_back(i);
+  Csr c;
+  c.ptr.assign(nz + 1, 0);
+  c.mptr.push_back(0);
+  for (auto& kv : by) {
+    const int z = kv.first / plane;
+    c.ptr[z + 1]++;
+    c.off.push_back(kv.first - z * plane);
+    c.vox.push_back(kv.first);
+    for (int m : kv.second) c.mem.push_back(m);
+    c.mptr.push_back((int)c.mem.size());
+  }
+  for (int z = 0; z < nz; ++z) c.ptr[z + 1] += c.ptr[z];
+  return c;
+}
+
+std::vector<int> plane_ranges(const int32_t* sorted, int n, int nz, int plane) {
+  std::vector<int> ptr(nz + 1, 0);
+  for (int i = 0; i < n; ++i) ptr[sorted[i] / plane + 1]++;
+  for (int z = 0; z < nz; ++z) ptr[z + 1] += ptr[z];
+  return ptr;
+}
+
+struct Layout {
+  size_t total = 0;
+  size_t add(size_t bytes) {
+    const size_t o = total;
+    total += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------ the plan
+struct fwi_plan {
+  fwi_problem prob;     // scalars (pointers cleared)
+  int K;                // max shots
+  int hx, npair, nxp, hxp, mspec, plane;
+  int64_t nvox;
+  AxisPlan ax, ay, az;
+  int ept_plane, ept_zmom, ept_zmass;
+  size_t smem_mom, smem_mass, smem_zmom, smem_zmass;
+  // host tables
+  std::vector<float2> tw, ap[3], am[3];
+  std::vector<float> kx2, ky2, kz2, lam[3], lams[3], wavelet;
+  Csr us, ur, rr;
+  std::vector<int> lay_ptr, gam_ptr, lay_idx, gam_idx;
+  int n_us, n_ur;
+  // workspace offsets
+  Layout L;
+  size_t o_tw, o_kx2, o_ky2, o_kz2, o_ap[3], o_am[3], o_lam[3], o_lams[3];
+  size_t o_us_ptr, o_us_off, o_us_vox, o_us_mptr, o_us_mem;
+  size_t o_ur_ptr, o_ur_off, o_ur_vox, o_ur_mptr, o_ur_mem;
+  size_t o_rr_ptr, o_rr_off, o_rr_col, o_lay_ptr, o_lay_idx, o_gam_ptr, o_gam_idx, o_wav;
+  size_t o_bad, o_c2, o_us_coef, o_ur_coef, o_coefG, o_inv3c2, o_amp, o_traces, o_obs, o_qf,
+      o_ghist, o_ring, o_pa, o_acc, o_dpart;
+  size_t o_sims, sim_bytes, sim_field, sim_spec;
+  int nblk_misfit;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t last = nullptr;
+  bool used = false;
+};
+
+namespace {
+
+template <typename T>
+T* at(fwi_plan* p, size_t off) { return reinterpret_cast<T*>(p->ws + off); }
+
+void sim_ptrs(fwi_plan* p, int s, SimPtrs* out, int role, int shot) {
+  char* base = p->ws + p->o_sims + (size_t)s * p->sim_bytes;
+  for (int c = 0; c < 3; ++c) {
+    out->v[c] = reinterpret_cast<float*>(base + c * p->sim_field);
+    out->rho[c] = reinterpret_cast<float*>(base + (3 + c) * p->sim_field);
+    out->spec[c] = reinterpret_cast<float2*>(base + 6 * p->sim_field + c * p->sim_spec);
+  }
+  out->role = role;
+  out->shot = shot;
+}
+
+void base_params(fwi_plan* p, StepParams* P) {
+  std::memset(P, 0, sizeof(*P));
+  const fwi_problem& q = p->prob;
+  P->nx = q.nx; P->ny = q.ny; P->nz = q.nz;
+  P->hx = p->hx; P->npair = p->npair; P->nxp = p->nxp; P->hxp = p->hxp;
+  P->nvox = p->nvox; P->plane = p->plane; P->mspec = p->mspec; P->nt = q.nt;
+  P->n_rec = q.n_rec; P->n_layer = q.n_layer; P->n_gamma = q.n_gamma;
+  P->n_us = p->n_us; P->n_ur = p->n_ur;
+  P->ax = p->ax; P->ay = p->ay; P->az = p->az;
+  P->tw = at<float2>(p, p->o_tw);
+  P->kx2 = at<float>(p, p->o_kx2); P->ky2 = at<float>(p, p->o_ky2); P->kz2 = at<float>(p, p->o_kz2);
+  for (int c = 0; c < 3; ++c) {
+    P->ap[c] = at<float2>(p, p->o_ap[c]);
+    P->am[c] = at<float2>(p, p->o_am[c]);
+    P->lam[c] = at<float>(p, p->o_lam[c]);
+    P->lams[c] = at<float>(p, p->o_lams[c]);
+  }
+  P->half_cdt = (float)(q.c_ref * q.dt / 2.0);
+  P->inv_n = (float)(1.0 / (double)p->nvox);
+  P->dt_over_rho0 = (float)(q.dt / q.rho0);
+  P->dt_rho0 = (float)(q.dt * q.rho0);
+  P->c2 = at<float>(p, p->o_c2);
+  P->bad = at<int>(p, p->o_bad);
+  P->us_ptr = at<int>(p, p->o_us_ptr); P->us_off = at<int>(p, p->o_us_off);
+  P->amp_src = at<float>(p, p->o_amp);
+  P->ur_ptr = at<int>(p, p->o_ur_ptr); P->ur_off = at<int>(p, p->o_ur_off);
+  P->ur_mptr = at<int>(p, p->o_ur_mptr); P->ur_mem = at<int>(p, p->o_ur_mem);
+  P->ur_coef = at<float>(p, p->o_ur_coef);
+  P->qf = at<float>(p, p->o_qf);
+  P->rr_ptr = at<int>(p, p->o_rr_ptr); P->rr_off = at<int>(p, p->o_rr_off);
+  P->rr_col = at<int>(p, p->o_rr_col);
+  P->traces = at<float>(p, p->o_traces);
+  P->lay_ptr = at<int>(p, p->o_lay_ptr); P->lay_idx = at<int>(p, p->o_lay_idx);
+  P->ghist = at<float>(p, p->o_ghist);
+  P->inv3c2 = at<float>(p, p->o_inv3c2);
+  P->gam_ptr = at<int>(p, p->o_gam_ptr); P->gam_idx = at<int>(p, p->o_gam_idx);
+  P->pa = at<float>(p, p->o_pa);
+  P->ring = at<float>(p, p->o_ring);
+}
+
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return FWI_ECUDA;    \
+  } while (0)
+
+template <int EPT>
+void set_attrs_plane(fwi_plan* p) {
+  cudaFuncSetAttribute(k_plane_mom<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_mom);
+  cudaFuncSetAttribute(k_plane_mass<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_mass);
+  cudaFuncSetAttribute(k_tr_init<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_mom);
+}
+template <int EPT>
+void set_attrs_z(fwi_plan* p) {
+  cudaFuncSetAttribute(k_zpass<0, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmom);
+  cudaFuncSetAttribute(k_zpass<1, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmass);
+}
+
+constexpr int kEpt = 8;   // complex values staged per thread per FFT pass
+#define EPT_SWITCH(ept, CALL) \
+  {                           \
+    constexpr int E = kEpt;   \
+    (void)(ept);              \
+    CALL;                     \
+  }
+
+void launch_step(fwi_plan* p, const StepParams& P, cudaStream_t st) {
+  const dim3 gz((p->mspec + kZTile - 1) / kZTile, P.nsims);
+  const dim3 gp(p->prob.nz, P.nsims);
+  EPT_SWITCH(p->ept_zmom, (k_zpass<0, E><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+  EPT_SWITCH(p->ept_plane, (k_plane_mom<E><<<gp, kTpbPlane, p->smem_mom, st>>>(P)));
+  EPT_SWITCH(p->ept_zmass, (k_zpass<1, E><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+  EPT_SWITCH(p->ept_plane, (k_plane_mass<E><<<gp, kTpbPlane, p->smem_mass, st>>>(P)));
+}
+
+fwi_status zero_sim(fwi_plan* p, int s, cudaStream_t st) {
+  CK(cudaMemsetAsync(p->ws + p->o_sims + (size_t)s * p->sim_bytes, 0, p->sim_bytes, st));
+  return FWI_OK;
+}
+
+// common per-call preparation: c^2, range flag, sparse coefficients
+fwi_status prepare(fwi_plan* p, const float* c, cudaStream_t st) {
+  const fwi_problem& q = p->prob;
+  CK(cudaMemsetAsync(p->ws + p->o_bad, 0, sizeof(int), st));
+  k_prepare_c<<<592, 256, 0, st>>>(c, at<float>(p, p->o_c2), p->nvox, (float)q.c_ref, at<int>(p, p->o_bad));
+  k_prepare_coefs<<<148, 256, 0, st>>>(c, q.dt, q.dx, at<int>(p, p->o_us_vox), p->n_us,
+                                       at<float>(p, p->o_us_coef), at<int>(p, p->o_ur_vox), p->n_ur,
+                                       at<float>(p, p->o_ur_coef), at<int>(p, p->o_gam_idx), q.n_gamma,
+                                       at<float>(p, p->o_coefG), at<int>(p, p->o_lay_idx), q.n_layer,
+                                       at<float>(p, p->o_inv3c2));
+  CK(cudaGetLastError());
+  return FWI_OK;
+}
+
+fwi_status run_forward(fwi_plan* p, const float* w, int K, bool record_layer, float* traces,
+                       cudaStream_t st) {
+  const fwi_problem& q = p->prob;
+  k_source_amp<<<dim3(q.nt, K), 128, 0, st>>>(w, q.n_src, at<float>(p, p->o_us_coef),
+                                              at<int>(p, p->o_us_mptr), at<int>(p, p->o_us_mem), p->n_us,
+                                              at<float>(p, p->o_wav), q.nt, at<float>(p, p->o_amp));
+  StepParams P;
+  base_params(p, &P);
+  P.record_layer = record_layer ? 1 : 0;
+  P.traces = traces;
+  P.nsims = K;
+  for (int k = 0; k < K; ++k) {
+    sim_ptrs(p, k, &P.sims[k], ROLE_FORWARD, k);
+    fwi_status s = zero_sim(p, k, st);
+    if (s != FWI_OK) return s;
+  }
+  for (int n = 0; n < q.nt; ++n) {
+    for (int k = 0; k < K; ++k) P.tidx[k] = n;
+    launch_step(p, P, st);
+  }
+  CK(cudaGetLastError());
+  return FWI_OK;
+}
+
+fwi_status check_call(fwi_plan* p, int K) {
+  if (!p || !p->ws) return FWI_EINVAL;
+  if (K < 1 || K > p->K) return FWI_EINVAL;
+  return FWI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fwi_status_string(fwi_status s) {
+  switch (s) {
+    case FWI_OK: return "ok";
+    case FWI_EINVAL: return "invalid argument";
+    case FWI_ENOMEM: return "out of memory / workspace too small";
+    case FWI_EUNSTABLE: return "sound speed outside (0, c_ref]: unstable";
+    case FWI_ETIMEOUT: return "device wait timed out";
+    case FWI_ECUDA: return "CUDA error";
+    case FWI_ECANCELLED: return "cancelled";
+    case FWI_ENOTSUP: return "grid not supported";
+  }
+  return "unknown status";
+}
+
+fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi_plan** out) {
+  if (!prob || !workspace_bytes || !out) return FWI_EINVAL;
+  const fwi_problem& q = *prob;
+  if (q.nx < 2 || q.ny < 2 || q.nz < 2 || q.nt < 3 || q.n_src < 1 || q.n_rec < 1 ||
+      q.n_gamma < 1 || q.n_layer < 0 || q.max_shots < 1 || q.max_shots > kMaxSims / 2)
+    return FWI_EINVAL;
+  if (!(q.dx > 0) || !(q.dt > 0) || !(q.c_ref > 0) || !(q.rho0 > 0) || q.pml_alpha < 0 || q.c_rec < 0)
+    return FWI_EINVAL;
+  if (!q.src_idx || !q.rec_idx || !q.gamma_idx || (q.n_layer > 0 && !q.layer_idx) || !q.wavelet)
+    return FWI_EINVAL;
+  if (q.pairing != FWI_PAIRING_LITERAL && q.pairing != FWI_PAIRING_EXACT) return FWI_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    const int n = a == 0 ? q.nx : (a == 1 ? q.ny : q.nz);
+    if (q.pml[a] < 0 || 2 * q.pml[a] > n) return FWI_EINVAL;
+  }
+  const int64_t nvox = (int64_t)q.nx * q.ny * q.nz;
+  if (nvox >= (int64_t)1 << 31) return FWI_ENOTSUP;
+  auto in_range = [&](const int32_t* v, int n) {
+    for (int i = 0; i < n; ++i)
+      if (v[i] < 0 || v[i] >= nvox) return false;
+    return true;
+  };
+  if (!in_range(q.src_idx, q.n_src) || !in_range(q.rec_idx, q.n_rec) ||
+      !in_range(q.gamma_idx, q.n_gamma) || !in_range(q.layer_idx, q.n_layer))
+    return FWI_EINVAL;
+  for (int i = 1; i < q.n_gamma; ++i)
+    if (q.gamma_idx[i] <= q.gamma_idx[i - 1]) return FWI_EINVAL;
+  for (int i = 1; i < q.n_layer; ++i)
+    if (q.layer_idx[i] <= q.layer_idx[i - 1]) return FWI_EINVAL;
+  for (int i = 0; i < q.n_layer; ++i)
+    if (!std::binary_search(q.gamma_idx, q.gamma_idx + q.n_gamma, q.layer_idx[i])) return FWI_EINVAL;
+
+  fwi_plan* p = new (std::nothrow) fwi_plan();
+  if (!p) return FWI_ENOMEM;
+  p->prob = q;
+  p->prob.src_idx = p->prob.rec_idx = p->prob.layer_idx = p->prob.gamma_idx = nullptr;
+  p->prob.wavelet = nullptr;
+  p->K = q.max_shots;
+  p->nvox = nvox;
+  p->hx = q.nx / 2 + 1;
+  p->npair = (q.ny + 1) / 2;
+  p->nxp = q.nx;
+  p->hxp = p->hx;
+  p->plane = q.nx * q.ny;
+  p->mspec = p->hx * q.ny;
+  if (!factor235(q.nx, &p->ax) || !factor235(q.ny, &p->ay) || !factor235(q.nz, &p->az)) {
+    delete p;
+    return FWI_ENOTSUP;
+  }
+  // twiddles W[k] = exp(-2 pi i k / N), per axis, FP64 -> FP32
+  AxisPlan* axes[3] = {&p->ax, &p->ay, &p->az};
+  for (int a = 0; a < 3; ++a) {
+    axes[a]->tw_off = (int)p->tw.size();
+    const int n = axes[a]->n;
+    for (int k = 0; k < n; ++k) {
+      const double ang = -2.0 * kPi * (double)k / (double)n;
+      p->tw.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+    }
+  }
+  // wavenumbers and the staggered x/y/z factors i k exp(+-i k dx/2) (Eq. 19)
+  const int lens[3] = {p->hx, q.ny, q.nz};
+  const int ns[3] = {q.nx, q.ny, q.nz};
+  std::vector<float>* k2[3] = {&p->kx2, &p->ky2, &p->kz2};
+  for (int a = 0; a < 3; ++a) {
+    for (int j = 0; j < lens[a]; ++j) {
+      const double k = wavenumber(j, ns[a], q.dx);
+      k2[a]->push_back((float)(k * k));
+      const double h = k * q.dx / 2.0;
+      // i k (cos h +- i sin h) = (-+ k sin h) + i k cos h
+      p->ap[a].push_back(make_float2((float)(-k * std::sin(h)), (float)(k * std::cos(h))));
+      p->am[a].push_back(make_float2((float)(k * std::sin(h)), (float)(k * std::cos(h))));
+    }
+    for (int i = 0; i < ns[a]; ++i) {
+      p->lam[a].push_back((float)pml_value(i, ns[a], q.pml[a], q.pml_alpha, q.c_ref, q.dx, q.dt, false));
+      p->lams[a].push_back((float)pml_value(i, ns[a], q.pml[a], q.pml_alpha, q.c_ref, q.dx, q.dt, true));
+    }
+  }
+  p->wavelet.assign(prob->wavelet, prob->wavelet + q.nt);
+  p->us = build_unique(prob->src_idx, q.n_src, q.nz, p->plane);
+  p->ur = build_unique(prob->rec_idx, q.n_rec, q.nz, p->plane);
+  p->n_us = (int)p->us.off.size();
+  p->n_ur = (int)p->ur.off.size();
+  // receivers to record, grouped by plane, keeping their column
+  {
+    std::vector<std::pair<int, int>> e;
+    for (int r = 0; r < q.n_rec; ++r) e.push_back({prob->rec_idx[r], r});
+    std::stable_sort(e.begin(), e.end());
+    p->rr.ptr.assign(q.nz + 1, 0);
+    for (auto& v : e) {
+      const int z = v.first / p->plane;
+      p->rr.ptr[z + 1]++;
+      p->rr.off.push_back(v.first - z * p->plane);
+      p->rr.mem.push_back(v.second);
+    }
+    for (int z = 0; z < q.nz; ++z) p->rr.ptr[z + 1] += p->rr.ptr[z];
+  }
+  p->lay_idx.assign(prob->layer_idx, prob->layer_idx + q.n_layer);
+  p->gam_idx.assign(prob->gamma_idx, prob->gamma_idx + q.n_gamma);
+  p->lay_ptr = plane_ranges(prob->layer_idx, q.n_layer, q.nz, p->plane);
+  p->gam_ptr = plane_ranges(prob->gamma_idx, q.n_gamma, q.nz, p->plane);
+
+  // launch shapes
+  const size_t plane_elems = std::max((size_t)p->npair * p->nxp, (size_t)q.ny * p->hxp);
+  p->ept_plane = p->ept_zmom = p->ept_zmass = 8;
+  p->smem_mom = plane_elems * sizeof(float2);
+  p->smem_mass = p->smem_mom + (size_t)p->plane * sizeof(float);
+  p->smem_zmom = (size_t)2 * kZTile * q.nz * sizeof(float2);
+  p->smem_zmass = (size_t)3 * kZTile * q.nz * sizeof(float2);
+  if (std::max(q.nx, std::max(q.ny, q.nz)) > 8 * kTpbZ || p->smem_mass > 227 * 1024 ||
+      p->smem_zmass > 227 * 1024) {
+    delete p;
+    return FWI_ENOTSUP;
+  }
+
+  // workspace layout
+  Layout& L = p->L;
+  const int K = p->K, nt = q.nt;
+  p->o_tw = L.add(p->tw.size() * sizeof(float2));
+  p->o_kx2 = L.add(p->kx2.size() * 4); p->o_ky2 = L.add(p->ky2.size() * 4); p->o_kz2 = L.add(p->kz2.size() * 4);
+  for (int a = 0; a < 3; ++a) {
+    p->o_ap[a] = L.add(p->ap[a].size() * sizeof(float2));
+    p->o_am[a] = L.add(p->am[a].size() * sizeof(float2));
+    p->o_lam[a] = L.add(p->lam[a].size() * 4);
+    p->o_lams[a] = L.add(p->lams[a].size() * 4);
+  }
+  p->o_us_ptr = L.add((q.nz + 1) * 4); p->o_us_off = L.add(p->n_us * 4); p->o_us_vox = L.add(p->n_us * 4);
+  p->o_us_mptr = L.add((p->n_us + 1) * 4); p->o_us_mem = L.add(q.n_src * 4);
+  p->o_ur_ptr = L.add((q.nz + 1) * 4); p->o_ur_off = L.add(p->n_ur * 4); p->o_ur_vox = L.add(p->n_ur * 4);
+  p->o_ur_mptr = L.add((p->n_ur + 1) * 4); p->o_ur_mem = L.add(q.n_rec * 4);
+  p->o_rr_ptr = L.add((q.nz + 1) * 4); p->o_rr_off = L.add(q.n_rec * 4); p->o_rr_col = L.add(q.n_rec * 4);
+  p->o_lay_ptr = L.add((q.nz + 1) * 4); p->o_lay_idx = L.add((size_t)q.n_layer * 4 + 4);
+  p->o_gam_ptr = L.add((q.nz + 1) * 4); p->o_gam_idx = L.add((size_t)q.n_gamma * 4);
+  p->o_wav = L.add((size_t)nt * 4);
+  p->o_bad = L.add(4);
+  p->o_c2 = L.add((size_t)nvox * 4);
+  p->o_us_coef = L.add(p->n_us * 4); p->o_ur_coef = L.add(p->n_ur * 4);
+  p->o_coefG = L.add((size_t)q.n_gamma * 4); p->o_inv3c2 = L.add((size_t)q.n_layer * 4 + 4);
+  p->o_amp = L.add((size_t)K * nt * p->n_us * 4);
+  p->o_traces = L.add((size_t)K * nt * q.n_rec * 4);
+  p->o_obs = L.add((size_t)K * nt * q.n_rec * 4);
+  p->o_qf = L.add((size_t)K * nt * q.n_rec * 4);
+  p->o_ghist = L.add((size_t)K * nt * q.n_layer * 4 + 4);
+  p->o_ring = L.add((size_t)K * 3 * q.n_gamma * 4);
+  p->o_pa = L.add((size_t)K * q.n_gamma * 4);
+  p->o_acc = L.add((size_t)K * q.n_gamma * 8);
+  p->nblk_misfit = (q.n_rec + 255) / 256;
+  p->o_dpart = L.add((size_t)K * p->nblk_misfit * 8);
+  p->sim_field = ((size_t)nvox * 4 + 255) & ~size_t(255);
+  p->sim_spec = ((size_t)p->mspec * q.nz * sizeof(float2) + 255) & ~size_t(255);
+  p->sim_bytes = 6 * p->sim_field + 3 * p->sim_spec;
+  p->o_sims = L.add((size_t)2 * K * p->sim_bytes);
+  *workspace_bytes = L.total;
+  *out = p;
+  return FWI_OK;
+}
+
+fwi_status fwi_plan_bind_workspace(fwi_plan* p, void* dev_ptr, size_t bytes) {
+  if (!p || !dev_ptr || ((uintptr_t)dev_ptr & 255)) return FWI_EINVAL;
+  if (bytes < p->L.total) return FWI_ENOMEM;
+  p->ws = static_cast<char*>(dev_ptr);
+  p->ws_bytes = bytes;
+  auto up = [&](size_t off, const void* src, size_t n) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpy(p->ws + off, src, n, cudaMemcpyHostToDevice);
+  };
+  CK(up(p->o_tw, p->tw.data(), p->tw.size() * sizeof(float2)));
+  CK(up(p->o_kx2, p->kx2.data(), p->kx2.size() * 4));
+  CK(up(p->o_ky2, p->ky2.data(), p->ky2.size() * 4));
+  CK(up(p->o_kz2, p->kz2.data(), p->kz2.size() * 4));
+  for (int a = 0; a < 3; ++a) {
+    CK(up(p->o_ap[a], p->ap[a].data(), p->ap[a].size() * sizeof(float2)));
+    CK(up(p->o_am[a], p->am[a].data(), p->am[a].size() * sizeof(float2)));
+    CK(up(p->o_lam[a], p->lam[a].data(), p->lam[a].size() * 4));
+    CK(up(p->o_lams[a], p->lams[a].data(), p->lams[a].size() * 4));
+  }
+  CK(up(p->o_us_ptr, p->us.ptr.data(), p->us.ptr.size() * 4));
+  CK(up(p->o_us_off, p->us.off.data(), p->us.off.size() * 4));
+  CK(up(p->o_us_vox, p->us.vox.data(), p->us.vox.size() * 4));
+  CK(up(p->o_us_mptr, p->us.mptr.data(), p->us.mptr.size() * 4));
+  CK(up(p->o_us_mem, p->us.mem.data(), p->us.mem.size() * 4));
+  CK(up(p->o_ur_ptr, p->ur.ptr.data(), p->ur.ptr.size() * 4));
+  CK(up(p->o_ur_off, p->ur.off.data(), p->ur.off.size() * 4));
+  CK(up(p->o_ur_vox, p->ur.vox.data(), p->ur.vox.size() * 4));
+  CK(up(p->o_ur_mptr, p->ur.mptr.data(), p->ur.mptr.size() * 4));
+  CK(up(p->o_ur_mem, p->ur.mem.data(), p->ur.mem.size() * 4));
+  CK(up(p->o_rr_ptr, p->rr.ptr.data(), p->rr.ptr.size() * 4));
+  CK(up(p->o_rr_off, p->rr.off.data(), p->rr.off.size() * 4));
+  CK(up(p->o_rr_col, p->rr.mem.data(), p->rr.mem.size() * 4));
+  CK(up(p->o_lay_ptr, p->lay_ptr.data(), p->lay_ptr.size() * 4));
+  CK(up(p->o_lay_idx, p->lay_idx.data(), p->lay_idx.size() * 4));
+  CK(up(p->o_gam_ptr, p->gam_ptr.data(), p->gam_ptr.size() * 4));
+  CK(up(p->o_gam_idx, p->gam_idx.data(), p->gam_idx.size() * 4));
+  CK(up(p->o_wav, p->wavelet.data(), p->wavelet.size() * 4));
+  EPT_SWITCH(p->ept_plane, set_attrs_plane<E>(p));
+  EPT_SWITCH(p->ept_zmom, set_attrs_z<E>(p));
+  EPT_SWITCH(p->ept_zmass, set_attrs_z<E>(p));
+  CK(cudaGetLastError());
+  return FWI_OK;
+}
+
+fwi_status fwi_forward(fwi_plan* p, const float* c, const float* weights, int32_t K, float* traces,
+                       void* stream) {
+  fwi_status s = check_call(p, K);
+  if (s != FWI_OK) return s;
+  if (!c || !weights || !traces) return FWI_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  p->last = st;
+  p->used = true;
+  if ((s = prepare(p, c, st)) != FWI_OK) return s;
+  return run_forward(p, weights, K, false, traces, st);
+}
+
+fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32_t K,
+                        const float* observed, int32_t observed_encoded, double* misfit, double* grad,
+                        float* traces, void* stream) {
+  fwi_status s = check_call(p, K);
+  if (s != FWI_OK) return s;
+  if (!c || !weights || !observed || !misfit || !grad) return FWI_EINVAL;
+  const fwi_problem& q = p->prob;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  p->last = st;
+  p->used = true;
+  const int nt = q.nt, Nt = nt - 1;
+  if ((s = prepare(p, c, st)) != FWI_OK) return s;
+  // observed data, encoded
+  const float* obs = observed;
+  if (!observed_encoded) {
+    const int64_t per = (int64_t)nt * q.n_rec;
+    k_encode<<<592, 256, 0, st>>>(observed, weights, q.n_src, K, per, at<float>(p, p->o_obs));
+    obs = at<float>(p, p->o_obs);
+  }
+  // forward, recording traces and the boundary-layer history
+  if ((s = run_forward(p, weights, K, true, at<float>(p, p->o_traces), st)) != FWI_OK) return s;
+  // residual, misfit, cumulative sum
+  k_misfit<<<dim3(p->nblk_misfit, K), 256, 0, st>>>(at<float>(p, p->o_traces), obs, nt, q.n_rec,
+                                                    at<float>(p, p->o_qf), at<double>(p, p->o_dpart));
+  k_misfit_final<<<1, 32, 0, st>>>(at<double>(p, p->o_dpart), p->nblk_misfit, K, misfit);
+  CK(cudaMemsetAsync(p->ws + p->o_acc, 0, (size_t)K * q.n_gamma * 8, st));
+  // adjoint sims 0..K-1 and TR sims K..2K-1
+  StepParams P;
+  base_params(p, &P);
+  for (int k = 0; k < K; ++k) {
+    sim_ptrs(p, k, &P.sims[k], ROLE_ADJOINT, k);
+    sim_ptrs(p, K + k, &P.sims[K + k], ROLE_TR, k);
+    if ((s = zero_sim(p, k, st)) != FWI_OK) return s;
+    if ((s = zero_sim(p, K + k, st)) != FWI_OK) return s;
+  }
+  // TR initial value and the lead TR step (m = 1)
+  StepParams T = P;
+  T.nsims = K;
+  for (int k = 0; k < K; ++k) {
+    T.sims[k] = P.sims[K + k];
+    T.tidx[k] = 1;
+    T.slot[k] = 1;
+  }
+  EPT_SWITCH(p->ept_plane, (k_tr_init<E><<<dim3(q.nz, K), kTpbPlane, p->smem_mom, st>>>(T)));
+  launch_step(p, T, st);
+  // interleaved adjoint and TR iterations
+  const bool exact = q.pairing == FWI_PAIRING_EXACT;
+  const int nit = exact ? Nt + 1 : Nt - 1;
+  const int nblk = (q.n_gamma + 255) / 256;
+  for (int it = 0; it < nit; ++it) {
+    const int qi = exact ? it : it + 1;    // row of Q injected by this adjoint step
+    const int m = it + 2;                  // TR state produced in this iteration
+    const int slot = m % 3;
+    StepParams S = P;
+    S.nsims = K;
+    for (int k = 0; k < K; ++k) S.tidx[k] = qi;
+    if (m <= Nt) {
+      S.nsims = 2 * K;
+      for (int k = 0; k < K; ++k) {
+        S.tidx[K + k] = m;
+        S.slot[K + k] = slot;
+      }
+    } else {
+      for (int k = 0; k < K; ++k)
+        CK(cudaMemsetAsync(at<float>(p, p->o_ring) + ((size_t)k * 3 + slot) * q.n_gamma, 0,
+                           (size_t)q.n_gamma * 4, st));
+    }
+    launch_step(p, S, st);
+    k_accumulate<<<dim3(nblk, K), 256, 0, st>>>(at<float>(p, p->o_ring), at<float>(p, p->o_pa),
+                                                at<float>(p, p->o_coefG), q.n_gamma, it % 3, (it + 1) % 3,
+                                                (it + 2) % 3, at<double>(p, p->o_acc), at<int>(p, p->o_bad));
+  }
+  // mean over shots, scaled to dD/dc if requested
+  const double scale = q.c_rec > 0 ? q.dx * q.c_rec / 2.0 : 1.0;
+  CK(cudaMemsetAsync(grad, 0, (size_t)p->nvox * 8, st));
+  k_grad_final<<<(q.n_gamma + 255) / 256, 256, 0, st>>>(at<double>(p, p->o_acc), at<int>(p, p->o_gam_idx),
+                                                        q.n_gamma, K, scale, grad);
+  if (traces)
+    CK(cudaMemcpyAsync(traces, p->ws + p->o_traces, (size_t)K * nt * q.n_rec * 4,
+                       cudaMemcpyDeviceToDevice, st));
+  CK(cudaGetLastError());
+  return FWI_OK;
+}
+
+fwi_status fwi_plan_status(fwi_plan* p) {
+  if (!p || !p->ws) return FWI_EINVAL;
+  if (!p->used) return FWI_OK;
+  CK(cudaStreamSynchronize(p->last));
+  int bad = 0;
+  CK(cudaMemcpy(&bad, p->ws + p->o_bad, sizeof(int), cudaMemcpyDeviceToHost));
+  return bad ? FWI_EUNSTABLE : FWI_OK;
+}
+
+int64_t fwi_plan_voxel_steps(const fwi_plan* p, int32_t K, int32_t gradient) {
+  if (!p) return -1;
+  const int64_t nt = p->prob.nt, Nt = nt - 1;
+  int64_t steps = nt;
+  if (gradient) {
+    const bool exact = p->prob.pairing == FWI_PAIRING_EXACT;
+    steps += Nt;                                   // TR: lead step + loop steps with m <= Nt
+    steps += exact ? Nt + 1 : Nt - 1;              // adjoint
+  }
+  return steps * p->nvox * K;
+}
+
+int64_t fwi_plan_launches(const fwi_plan* p, int32_t K, int32_t gradient) {
+  if (!p) return -1;
+  const int64_t nt = p->prob.nt, Nt = nt - 1;
+  int64_t n = 2 + 1 + 4 * nt;                       // prepare x2, source amp, steps
+  if (gradient) {
+    const bool exact = p->prob.pairing == FWI_PAIRING_EXACT;
+    const int64_t nit = exact ? Nt + 1 : Nt - 1;
+    n += 2 + 1 + 4 + nit * 5 + 1;                   // misfit x2, tr init, lead step, loop, final
+  }
+  (void)K;
+  return n;
+}
+
+fwi_status fwi_plan_destroy(fwi_plan* p) {
+  delete p;
+  return FWI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+"""Thin Python binding of the C ABI in include/fwi.h (argument marshalling only).
+
+Every step of the hot path runs in libfwi.so's CUDA kernels; PyTorch only
+provides device memory and streams.  There is no CPU fallback: if the library
+is missing or cannot be loaded, every call raises.
+
+The functions fwi_plan_create ... fwi_status_string mirror the C entry points
+one to one; `Plan` is a convenience wrapper that owns the workspace tensor.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfwi.so")
+
+FWI_OK = 0
+FWI_EINVAL = 1
+FWI_ENOMEM = 2
+FWI_EUNSTABLE = 3
+FWI_ETIMEOUT = 4
+FWI_ECUDA = 5
+FWI_ECANCELLED = 6
+FWI_ENOTSUP = 7
+
+PAIRING = {"literal": 0, "exact": 1}
+
+C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_gradient",
+             "fwi_plan_status", "fwi_plan_voxel_steps", "fwi_plan_launches", "fwi_plan_destroy",
+             "fwi_status_string")
+
+
+class FwiError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {fwi_status_string(status)} (status {status})")
+
+
+class fwi_problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("pml", ctypes.c_int32 * 3),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("c_ref", ctypes.c_double),
+        ("rho0", ctypes.c_double), ("pml_alpha", ctypes.c_double), ("c_rec", ctypes.c_double),
+        ("nt", ctypes.c_int32), ("n_src", ctypes.c_int32), ("n_rec", ctypes.c_int32),
+        ("n_layer", ctypes.c_int32), ("n_gamma", ctypes.c_int32),
+        ("src_idx", ctypes.POINTER(ctypes.c_int32)), ("rec_idx", ctypes.POINTER(ctypes.c_int32)),
+        ("layer_idx", ctypes.POINTER(ctypes.c_int32)), ("gamma_idx", ctypes.POINTER(ctypes.c_int32)),
+        ("wavelet", ctypes.POINTER(ctypes.c_float)),
+        ("pairing", ctypes.c_int32), ("max_shots", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libfwi.so (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2102_00755_b300/build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        L.fwi_plan_create.argtypes = [ctypes.POINTER(fwi_problem), ctypes.POINTER(sz), ctypes.POINTER(vp)]
+        L.fwi_plan_create.restype = ctypes.c_int
+        L.fwi_plan_bind_workspace.argtypes = [vp, vp, sz]
+        L.fwi_plan_bind_workspace.restype = ctypes.c_int
+        L.fwi_forward.argtypes = [vp, vp, vp, i32, vp, vp]
+        L.fwi_forward.restype = ctypes.c_int
+        L.fwi_gradient.argtypes = [vp, vp, vp, i32, vp, i32, vp, vp, vp, vp]
+        L.fwi_gradient.restype = ctypes.c_int
+        L.fwi_plan_status.argtypes = [vp]
+        L.fwi_plan_status.restype = ctypes.c_int
+        L.fwi_plan_voxel_steps.argtypes = [vp, i32, i32]
+        L.fwi_plan_voxel_steps.restype = i64
+        L.fwi_plan_launches.argtypes = [vp, i32, i32]
+        L.fwi_plan_launches.restype = i64
+        L.fwi_plan_destroy.argtypes = [vp]
+        L.fwi_plan_destroy.restype = ctypes.c_int
+        L.fwi_status_string.argtypes = [ctypes.c_int]
+        L.fwi_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+# ---- one-to-one wrappers of the C entry points ---------------------------------------
+def fwi_status_string(status: int) -> str:
+    return lib().fwi_status_string(status).decode()
+
+
+def fwi_plan_create(prob: fwi_problem):
+    ws = ctypes.c_size_t(0)
+    plan = ctypes.c_void_p(0)
+    st = lib().fwi_plan_create(ctypes.byref(prob), ctypes.byref(ws), ctypes.byref(plan))
+    return st, plan, ws.value
+
+
+def fwi_plan_bind_workspace(plan, ptr: int, nbytes: int) -> int:
+    return lib().fwi_plan_bind_workspace(plan, ctypes.c_void_p(ptr), nbytes)
+
+
+def fwi_forward(plan, c_ptr, w_ptr, K, traces_ptr, stream) -> int:
+    return lib().fwi_forward(plan, c_ptr, w_ptr, K, traces_ptr, stream)
+
+
+def fwi_gradient(plan, c_ptr, w_ptr, K, obs_ptr, obs_encoded, misfit_ptr, grad_ptr, traces_ptr,
+                 stream) -> int:
+    return lib().fwi_gradient(plan, c_ptr, w_ptr, K, obs_ptr, obs_encoded, misfit_ptr, grad_ptr,
+                              traces_ptr, stream)
+
+
+def fwi_plan_status(plan) -> int:
+    return lib().fwi_plan_status(plan)
+
+
+def fwi_plan_voxel_steps(plan, K, gradient) -> int:
+    return lib().fwi_plan_voxel_steps(plan, K, gradient)
+
+
+def fwi_plan_launches(plan, K, gradient) -> int:
+    return lib().fwi_plan_launches(plan, K, gradient)
+
+
+def fwi_plan_destroy(plan) -> int:
+    return lib().fwi_plan_destroy(plan)
+
+
+# ---- convenience wrapper --------------------------------------------------------------
+def _i32(a):
+    import numpy as np
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _check(st, where):
+    if st != FWI_OK:
+        raise FwiError(st, where)
+
+
+def _stream_handle(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t: torch.Tensor, dtype, name):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A plan for one grid and transducer setup; owns its device workspace tensor.
+
+    Geometry comes from keyword arguments mirroring fwi_problem (index lists and
+    wavelet as host arrays).  `device` selects the CUDA device for the workspace.
+    """
+
+    def __init__(self, *, nx, ny, nz, pml, dx, dt, c_ref, rho0, pml_alpha, nt, src_idx, rec_idx,
+                 layer_idx, gamma_idx, wavelet, pairing="literal", max_shots=1, c_rec=0.0,
+                 device="cuda", workspace=None):
+        import numpy as np
+        self._keep = [_i32(src_idx), _i32(rec_idx), _i32(layer_idx), _i32(gamma_idx),
+                      np.ascontiguousarray(wavelet, dtype=np.float32)]
+        s, r, l, g, w = self._keep
+        P = fwi_problem()
+        P.nx, P.ny, P.nz = nx, ny, nz
+        P.pml[0], P.pml[1], P.pml[2] = pml
+        P.dx, P.dt, P.c_ref, P.rho0, P.pml_alpha, P.c_rec = dx, dt, c_ref, rho0, pml_alpha, c_rec
+        P.nt, P.n_src, P.n_rec, P.n_layer, P.n_gamma = nt, len(s), len(r), len(l), len(g)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        P.src_idx = s.ctypes.data_as(ip)
+        P.rec_idx = r.ctypes.data_as(ip)
+        P.layer_idx = l.ctypes.data_as(ip)
+        P.gamma_idx = g.ctypes.data_as(ip)
+        P.wavelet = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        P.pairing = PAIRING[pairing] if isinstance(pairing, str) else int(pairing)
+        P.max_shots = max_shots
+        self.prob = P
+        st, plan, nbytes = fwi_plan_create(P)
+        _check(st, "fwi_plan_create")
+        self.handle = plan
+        self.workspace_bytes = nbytes
+        self.nx, self.ny, self.nz, self.nt = nx, ny, nz, nt
+        self.n_src, self.n_rec, self.max_shots = len(s), len(r), max_shots
+        self.device = torch.device(device)
+        if workspace is None:
+            workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.workspace = workspace
+        base = workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        if aligned + nbytes > base + workspace.numel():
+            raise ValueError("workspace tensor too small")
+        with torch.cuda.device(self.device):
+            _check(fwi_plan_bind_workspace(plan, aligned, nbytes), "fwi_plan_bind_workspace")
+
+    @classmethod
+    def from_workload(cls, wl, *, pairing="literal", max_shots=None, c_rec=None, pml_on=True, **kw):
+        return cls(nx=wl.nx, ny=wl.ny, nz=wl.nz, pml=wl.pml if pml_on else (0, 0, 0), dx=wl.dx,
+                   dt=wl.dt, c_ref=wl.c_ref, rho0=wl.rho0, pml_alpha=wl.pml_alpha, nt=wl.nt,
+                   src_idx=wl.src_idx, rec_idx=wl.rec_idx, layer_idx=wl.layer_idx,
+                   gamma_idx=wl.gamma_idx, wavelet=wl.wavelet, pairing=pairing,
+                   max_shots=max_shots or len(wl.weights),
+                   c_rec=wl.c_rec if c_rec is None else c_rec, **kw)
+
+    @property
+    def n_vox(self):
+        return self.nx * self.ny * self.nz
+
+    def forward(self, c: torch.Tensor, weights: torch.Tensor, traces: torch.Tensor = None,
+                stream=None) -> torch.Tensor:
+        K = weights.shape[0]
+        if traces is None:
+            traces = torch.empty((K, self.nt, self.n_rec), dtype=torch.float32, device=c.device)
+        st = fwi_forward(self.handle, _dptr(c, torch.float32, "c"), _dptr(weights, torch.float32, "weights"),
+                         K, _dptr(traces, torch.float32, "traces"), _stream_handle(stream))
+        _check(st, "fwi_forward")
+        return traces
+
+    def gradient(self, c: torch.Tensor, weights: torch.Tensor, observed: torch.Tensor, encoded=True,
+                 misfit=None, grad=None, traces=None, stream=None):
+        K = weights.shape[0]
+        if misfit is None:
+            misfit = torch.empty(K, dtype=torch.float64, device=c.device)
+        if grad is None:
+            grad = torch.empty(self.n_vox, dtype=torch.float64, device=c.device)
+        tp = _dptr(traces, torch.float32, "traces") if traces is not None else ctypes.c_void_p(0)
+        st = fwi_gradient(self.handle, _dptr(c, torch.float32, "c"),
+                          _dptr(weights, torch.float32, "weights"), K,
+                          _dptr(observed, torch.float32, "observed"), 1 if encoded else 0,
+                          _dptr(misfit, torch.float64, "misfit"), _dptr(grad, torch.float64, "grad"),
+                          tp, _stream_handle(stream))
+        _check(st, "fwi_gradient")
+        return misfit, grad
+
+    def status(self) -> int:
+        return fwi_plan_status(self.handle)
+
+    def voxel_steps(self, K, gradient=True) -> int:
+        return fwi_plan_voxel_steps(self.handle, K, 1 if gradient else 0)
+
+    def launches(self, K, gradient=True) -> int:
+        return fwi_plan_launches(self.handle, K, 1 if gradient else 0)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fwi_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

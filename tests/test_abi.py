@@ -1,0 +1,110 @@
+"""Host-side checks of the C ABI: the library loads, exports every entry point that
+include/fwi.h declares, and rejects bad problems at plan creation (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2102_00755_b300 import build as fbuild
+from paper_2102_00755_b300 import fwi, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    fbuild.build()
+    return fwi.lib()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fwi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fwi_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(fwi.C_SYMBOLS)
+
+
+def test_status_strings(L):
+    for s in range(8):
+        assert fwi.fwi_status_string(s)
+    assert "unstable" in fwi.fwi_status_string(fwi.FWI_EUNSTABLE)
+
+
+def _problem(wl, **over):
+    keep = [np.ascontiguousarray(a, dtype=np.int32) for a in (wl.src_idx, wl.rec_idx, wl.layer_idx, wl.gamma_idx)]
+    wav = np.ascontiguousarray(wl.wavelet, dtype=np.float32)
+    P = fwi.fwi_problem()
+    P.nx, P.ny, P.nz = wl.nx, wl.ny, wl.nz
+    P.pml[0], P.pml[1], P.pml[2] = wl.pml
+    P.dx, P.dt, P.c_ref, P.rho0, P.pml_alpha, P.c_rec = wl.dx, wl.dt, wl.c_ref, wl.rho0, wl.pml_alpha, 0.0
+    P.nt, P.n_src, P.n_rec, P.n_layer, P.n_gamma = wl.nt, *[len(k) for k in keep]
+    ip = ctypes.POINTER(ctypes.c_int32)
+    P.src_idx, P.rec_idx, P.layer_idx, P.gamma_idx = [k.ctypes.data_as(ip) for k in keep]
+    P.wavelet = wav.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    P.pairing, P.max_shots = 0, 2
+    for k, v in over.items():
+        setattr(P, k, v)
+    return P, (keep, wav)
+
+
+def test_plan_create_reports_workspace(L):
+    wl = synth.small_workload(24, 20, 18, 40)
+    P, keep = _problem(wl)
+    st, plan, nbytes = fwi.fwi_plan_create(P)
+    assert st == fwi.FWI_OK and nbytes > 0
+    N = wl.n_vox
+    assert nbytes > 2 * 2 * 6 * N * 4          # 2K simulation states of six fields at least
+    assert fwi.fwi_plan_voxel_steps(plan, 2, 1) == 2 * N * (3 * wl.nt - 3)
+    assert fwi.fwi_plan_voxel_steps(plan, 1, 0) == N * wl.nt
+    fwi.fwi_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nx", 1), ("nt", 2), ("max_shots", 0), ("max_shots", 9), ("dx", 0.0), ("pairing", 5),
+    ("c_rec", -1.0)])
+def test_plan_create_rejects_bad_scalars(L, field, value):
+    wl = synth.small_workload(24, 20, 18, 40)
+    P, keep = _problem(wl, **{field: value})
+    st, plan, _ = fwi.fwi_plan_create(P)
+    assert st == fwi.FWI_EINVAL
+
+
+def test_plan_create_rejects_bad_lists(L):
+    wl = synth.small_workload(24, 20, 18, 40)
+    bad = synth.Workload(**{**wl.__dict__})
+    bad.rec_idx = wl.rec_idx.copy()
+    bad.rec_idx[0] = wl.n_vox          # out of range
+    P, keep = _problem(bad)
+    assert fwi.fwi_plan_create(P)[0] == fwi.FWI_EINVAL
+    bad = synth.Workload(**{**wl.__dict__})
+    bad.gamma_idx = wl.gamma_idx[::-1].copy()   # not increasing
+    P, keep = _problem(bad)
+    assert fwi.fwi_plan_create(P)[0] == fwi.FWI_EINVAL
+    bad = synth.Workload(**{**wl.__dict__})
+    bad.layer_idx = np.array([wl.src_idx[0]], np.int32)   # layer voxel outside Gamma
+    P, keep = _problem(bad)
+    assert fwi.fwi_plan_create(P)[0] == fwi.FWI_EINVAL
+
+
+def test_plan_create_rejects_unsupported_sizes(L):
+    wl = synth.small_workload(24, 20, 18, 40)
+    P, keep = _problem(wl, nx=21)        # 21 = 3 * 7: prime factor 7
+    # keep indices valid for the smaller grid
+    st, plan, _ = fwi.fwi_plan_create(P)
+    assert st in (fwi.FWI_ENOTSUP, fwi.FWI_EINVAL)
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    monkeypatch.setattr(fwi, "_lib", None)
+    monkeypatch.setattr(fwi, "LIB_PATH", "/nonexistent/libfwi.so")
+    with pytest.raises(ImportError):
+        fwi.lib()

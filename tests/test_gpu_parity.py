@@ -1,0 +1,137 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: traces rel l2 <= 1e-4, gradient rel l2 <= 1e-3 (FP32 fields over
+hundreds of steps against FP64), misfit rel <= 1e-3 (it is a difference of
+nearly equal traces squared).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2102_00755_b300 import build as fbuild
+from paper_2102_00755_b300 import fwi, synth
+
+from . import oracle_cases as oc
+
+pytestmark = pytest.mark.gpu
+
+TOL_TRACES = 1e-4
+TOL_GRAD = 1e-3
+TOL_MISFIT = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    fbuild.build()
+    fwi.lib()
+    assert torch.cuda.is_available()
+
+
+def dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def run_forward(wl, c, weights, pml_on=True):
+    plan = fwi.Plan.from_workload(wl, max_shots=len(weights), pml_on=pml_on)
+    tr = plan.forward(dev(c), dev(weights))
+    assert plan.status() == fwi.FWI_OK
+    return tr.cpu().numpy()
+
+
+def run_gradient(wl, f_obs, pairing, weights=None, pml_on=True, encoded=True, observed=None):
+    W = wl.weights if weights is None else weights
+    plan = fwi.Plan.from_workload(wl, pairing=pairing, max_shots=len(W), pml_on=pml_on)
+    traces = torch.empty((len(W), wl.nt, len(wl.rec_idx)), dtype=torch.float32, device="cuda")
+    obs = dev(f_obs if observed is None else observed)
+    D, g = plan.gradient(dev(wl.c_model), dev(W), obs, encoded=encoded, traces=traces)
+    assert plan.status() == fwi.FWI_OK
+    return traces.cpu().numpy(), D.cpu().numpy(), g.cpu().numpy().reshape(wl.shape)
+
+
+def test_forward_parity_small_ragged():
+    wl, f_obs = oc.small_case()
+    f_gpu = run_forward(wl, wl.c_true, wl.weights)
+    for k in range(len(wl.weights)):
+        assert oc.rel(f_gpu[k], f_obs[k]) < TOL_TRACES
+
+
+@pytest.mark.parametrize("shape", [(15, 9, 10), (27, 25, 12), (16, 15, 9), (30, 18, 25)])
+def test_forward_parity_odd_and_mixed_radix_shapes(shape):
+    wl = synth.small_workload(*shape, 40, pml=3, n_src=2, n_rec=12, K=1, seed=3)
+    ref = oc.forward(wl, wl.c_model, wl.weights)
+    f_gpu = run_forward(wl, wl.c_model, wl.weights)
+    assert oc.rel(f_gpu[0], ref[0]) < TOL_TRACES
+
+
+@pytest.mark.parametrize("pairing", ["literal", "exact"])
+def test_gradient_parity_small(pairing):
+    wl, f_obs = oc.small_case()
+    f_ref, D_ref, g_ref = oc.small_gradient(pairing)
+    f_gpu, D_gpu, g_gpu = run_gradient(wl, f_obs, pairing)
+    for k in range(len(wl.weights)):
+        assert oc.rel(f_gpu[k], f_ref[k]) < TOL_TRACES
+    assert np.all(np.abs(D_gpu - D_ref) <= TOL_MISFIT * np.abs(D_ref))
+    assert oc.rel(g_gpu, g_ref) < TOL_GRAD
+    gam = np.zeros(wl.n_vox, bool)
+    gam[wl.gamma_idx] = True
+    assert np.all(g_gpu.reshape(-1)[~gam] == 0.0)
+
+
+def test_gradient_raw_observed_is_encoded_on_device():
+    """observed_encoded = 0: per-source data encoded with the weights on the GPU."""
+    wl, _ = oc.small_case()
+    n_src = len(wl.src_idx)
+    raw = oc.observed(wl, weights=np.eye(n_src))            # [n_src, nt, n_rec]
+    enc = synth.f32(np.tensordot(wl.weights, raw, axes=1))
+    _, D1, g1 = run_gradient(wl, enc, "literal")
+    _, D2, g2 = run_gradient(wl, None, "literal", encoded=False, observed=raw)
+    assert oc.rel(g2, g1) < 1e-5
+    assert np.allclose(D2, D1, rtol=1e-5)
+
+
+@pytest.mark.parametrize("pairing", ["literal", "exact"])
+def test_config1_gradient_parity(pairing):
+    """The 32^3 one-source configuration, 300 steps, PML inside, both pairings."""
+    wl, f_obs = oc.config1_case()
+    f_ref, D_ref, g_ref = oc.config1_gradient(pairing)
+    f_gpu, D_gpu, g_gpu = run_gradient(wl, f_obs, pairing)
+    assert oc.rel(f_gpu[0], f_ref[0]) < TOL_TRACES
+    assert abs(D_gpu[0] - D_ref[0]) <= TOL_MISFIT * D_ref[0]
+    assert oc.rel(g_gpu, g_ref) < TOL_GRAD
+
+
+def test_config1_forward_parity_true_model():
+    wl, f_obs = oc.config1_case()
+    f_gpu = run_forward(wl, wl.c_true, wl.weights)
+    assert oc.rel(f_gpu[0], f_obs[0]) < TOL_TRACES
+
+
+def test_batched_shots_equal_single_shots():
+    """Each super-shot's result is the same alone and batched with others."""
+    wl, f_obs = oc.small_case()
+    _, D_b, _ = run_gradient(wl, f_obs, "literal")
+    f_b = run_forward(wl, wl.c_model, wl.weights)
+    for k in range(len(wl.weights)):
+        f_1 = run_forward(wl, wl.c_model, wl.weights[k:k + 1])
+        assert np.array_equal(f_1[0], f_b[k])
+        _, D_1, _ = run_gradient(wl, f_obs[k:k + 1], "literal", weights=wl.weights[k:k + 1])
+        assert D_1[0] == D_b[k]
+
+
+def test_unstable_sound_speed_is_reported():
+    wl, _ = oc.small_case()
+    plan = fwi.Plan.from_workload(wl)
+    c = wl.c_model.copy()
+    c.reshape(-1)[5] = 1900.0          # above c_ref = 1800
+    plan.forward(dev(c), dev(wl.weights[:1]))
+    assert plan.status() == fwi.FWI_EUNSTABLE
+    plan.forward(dev(wl.c_model), dev(wl.weights[:1]))
+    assert plan.status() == fwi.FWI_OK
+
+
+def test_call_argument_errors():
+    wl, _ = oc.small_case()
+    plan = fwi.Plan.from_workload(wl, max_shots=1)
+    with pytest.raises(fwi.FwiError) as e:
+        plan.forward(dev(wl.c_model), dev(wl.weights))     # K = 2 > max_shots
+    assert e.value.status == fwi.FWI_EINVAL
