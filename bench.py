@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the TR-based sound-speed gradient (forward + TR + adjoint simulations).
+
+One step = one fwi_gradient call on the 128 x 128 x 64 breast-phantom workload
+(256 emitters, 1024 receivers, 4 Rademacher-encoded super-shots, 1500 time
+samples, 10-cell PML, literal Alg. 1 pairing): 4 x (1500 + 1499 + 1498)
+simulation steps of 2^20 voxels.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on bounded samples of the same
+workload (the reference arm of this build; the paper ships no code).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gvoxel-steps/s and gradients/h vs plain form at rel l2<=1e-4; p50/p99 latency"
+UNIT = "Gvoxel-steps/s"
+WORKLOAD = ("plain method at scale: 128x128x64 breast phantom, 256 emitters + 1024 receivers, "
+            "4 Rademacher super-shots, 1500 steps, TR gradient (literal Alg. 1 pairing)")
+
+# Algorithmic DRAM bytes per voxel for one simulation in one launch (FP32 fields,
+# half spectra of hx*ny*nz complex FP32 = 8*hx/nx bytes per voxel each).
+def alg_bytes_per_voxel(kernel, nx):
+    hf = 8.0 * (nx // 2 + 1) / nx
+    return {"zpass_momentum": 3 * hf,             # read P_xy, write Q and R
+            "plane_momentum": 5 * hf + 24.0,      # read Q, R; write 3 V_xy; v_xi read + write
+            "zpass_mass": 6 * hf,                 # 3 spectra read + written
+            "plane_mass": 4 * hf + 28.0}[kernel]  # 3 spectra read, P_xy written; rho r/w; c0^2
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.fh.flush()
+        self.fh.seek(0)
+        rows = [r.split(",") for r in self.fh.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.fh.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(wl, budget_s=15.0, min_steps=6):
+    """Time the FP64 oracle's time step on the same grid (bounded sample)."""
+    workers = os.cpu_count() or 1
+    os.environ["ORACLE_WORKERS"] = str(workers)
+    from oracle import pstd
+    G = pstd.grid_for(wl)
+    S = pstd.State(G.shape)
+    c2 = wl.c_model ** 2
+    src = pstd.injection_map(G, wl.c_model, wl.src_idx, wl.weights[0])
+    pstd.step(G, S, c2, mass_src=src * wl.wavelet[0])      # warm-up (FFT plans)
+    t0 = time.perf_counter()
+    n = 0
+    while n < min_steps or time.perf_counter() - t0 < budget_s:
+        pstd.step(G, S, c2, mass_src=src * wl.wavelet[min(n + 1, wl.nt - 1)])
+        n += 1
+        if n >= 400:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": wl.n_vox * n / dt / 1e9, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{n} FP64 oracle time steps of one simulation on the {wl.nx}x{wl.ny}x{wl.nz} "
+                      f"grid ({dt:.1f} s); a gradient is 3 simulations of such steps"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on bounded samples of the same workload."""
+    from paper_2102_00755_b300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = synth.config2()
+    os.environ["ORACLE_WORKERS"] = str(os.cpu_count() or 1)
+    from oracle import pstd
+    G = pstd.grid_for(wl)
+    S = pstd.State(G.shape)
+    c2 = wl.c_model ** 2
+    src = pstd.injection_map(G, wl.c_model, wl.src_idx, wl.weights[0])
+    per_step = 4                      # oracle time steps per benchmark step (bounded sample)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for n in range(per_step):
+            pstd.step(G, S, c2, mass_src=src * wl.wavelet[(it * per_step + n) % wl.nt])
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = wl.n_vox * per_step * args.steps / tot / 1e9
+    sample = (f"{per_step} FP64 oracle time steps of one simulation per step on the "
+              f"{wl.nx}x{wl.ny}x{wl.nz} grid")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WORKLOAD, "grid": [wl.nx, wl.ny, wl.nz], "nt": wl.nt},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2102_00755_b300 import fwi, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    wl = synth.config2()
+    K = wl.weights.shape[0]
+    if rank > 0:   # independent estimates per GPU (Sec. 4.5): other encoding weights
+        rng = np.random.default_rng(1000 + rank)
+        wl.weights = np.stack([synth.rademacher(len(wl.src_idx), rng) for _ in range(K)])
+    plan = fwi.Plan.from_workload(wl, pairing="literal", max_shots=K, device=dev)
+    c_true = torch.tensor(wl.c_true, dtype=torch.float32, device=dev).reshape(-1)
+    c_model = torch.tensor(wl.c_model, dtype=torch.float32, device=dev).reshape(-1)
+    w = torch.tensor(wl.weights, dtype=torch.float32, device=dev)
+    # encoded observed data by linearity: forward of the encoded true model
+    observed = plan.forward(c_true, w)
+    misfit = torch.empty(K, dtype=torch.float64, device=dev)
+    grad = torch.empty(wl.n_vox, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    vsteps = plan.voxel_steps(K, True)
+    launches = plan.launches(K, True)
+
+    def step():
+        plan.gradient(c_model, w, observed, misfit=misfit, grad=grad)
+
+    # warm-up; the first warm-up step times every kernel (CUDA events) for the time shares
+    share_ms = {}
+    for i in range(args.warmup):
+        if i == 0:
+            plan.profile(enable=True)
+        step()
+        if i == 0:
+            plan.profile(enable=False)
+            share_ms = {k: v[0] for k, v in plan.profile_read().items()}
+        flush.zero_()
+    torch.cuda.synchronize(dev)
+    if plan.status() != fwi.FWI_OK:
+        raise RuntimeError("gradient failed: " + fwi.fwi_status_string(plan.status()))
+    dominant = max(share_ms, key=share_ms.get)
+
+    # timed region (device events around each step; L2 flushed between steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    plan.profile(dominant, enable=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    plan.profile(dominant, enable=False)
+    kern_ms, kern_launches, kern_sims = plan.profile_read()[dominant]
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = vsteps * world * args.steps / (tot_ms / 1e3) / 1e9
+    grads_per_h = 3600.0 * world * args.steps / (tot_ms / 1e3)
+    clocks = clk.summary()
+    assert plan.status() == fwi.FWI_OK
+
+    # roofline of the dominant kernel over the timed region
+    hbm, kind = peaks()
+    bpv = alg_bytes_per_voxel(dominant, wl.nx)
+    alg_bytes = bpv * wl.n_vox * kern_sims
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm,
+                "peak_kind": kind, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+                "traffic": None, "alg_bytes_per_voxel": bpv,
+                "avg_launch_ms": kern_ms / max(kern_launches, 1), "launches_timed": kern_launches,
+                "kernel_share_of_step": {k: v / sum(share_ms.values()) for k, v in share_ms.items()}}
+
+    # plain form: one simulation per launch sequence, same work
+    plain = None
+    if args.plain_steps > 0:
+        pplan = fwi.Plan.from_workload(wl, pairing="literal", max_shots=K, sims_per_launch=1, device=dev)
+        pplan.gradient(c_model, w, observed, misfit=misfit, grad=grad)
+        torch.cuda.synchronize(dev)
+        pt = []
+        for i in range(args.plain_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pplan.gradient(c_model, w, observed, misfit=misfit, grad=grad)
+            b.record(stream)
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            pt.append(a.elapsed_time(b))
+        pms = sum(pt) / len(pt)
+        plain = {"value": vsteps / (pms / 1e3) / 1e9, "unit": UNIT,
+                 "gradients_per_h": 3600.0 / (pms / 1e3), "ms_per_step": pms,
+                 "form": "one simulation per launch sequence (sims_per_launch = 1)"}
+        pplan.close()
+        del pplan
+
+    # end to end through the public API with host buffers (pinned), copies inside
+    e2e = None
+    if args.e2e_steps > 0:
+        hc = c_model.cpu().pin_memory()
+        hw = w.cpu().pin_memory()
+        ho = observed.cpu().pin_memory()
+        hm = torch.empty(K, dtype=torch.float64).pin_memory()
+        hg = torch.empty(wl.n_vox, dtype=torch.float64).pin_memory()
+        et = []
+        for i in range(args.e2e_steps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dc = hc.to(dev, non_blocking=True)
+            dw = hw.to(dev, non_blocking=True)
+            do = ho.to(dev, non_blocking=True)
+            m, g = plan.gradient(dc, dw, do)
+            hm.copy_(m, non_blocking=True)
+            hg.copy_(g, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            if i > 0:
+                et.append(a.elapsed_time(b))
+            flush.zero_()
+        ems = sum(et) / len(et)
+        if world > 1:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        h2d = hc.numel() * 4 + hw.numel() * 4 + ho.numel() * 4
+        e2e = {"value": vsteps * world / (ems / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": hm.numel() * 8 + hg.numel() * 8, "ms_per_step": ems,
+               "gradients_per_h": 3600.0 * world / (ems / 1e3)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(wl)
+    sorted_ms = sorted(step_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [wl.nx, wl.ny, wl.nz], "nt": wl.nt,
+                   "super_shots": K, "n_src": int(len(wl.src_idx)), "n_rec": int(len(wl.rec_idx)),
+                   "n_gamma": int(len(wl.gamma_idx)), "n_layer": int(len(wl.layer_idx)),
+                   "pairing": "literal", "voxel_steps_per_step": vsteps,
+                   "l2": "256 MB buffer written between timed steps; working set > 126 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gradients_per_h": grads_per_h,
+        "latency_ms": {"p50": float(np.percentile(sorted_ms, 50)), "p99": float(np.percentile(sorted_ms, 99))},
+        "plain": plain,
+        "batched_vs_plain": (value / plain["value"]) if plain else None,
+        "e2e": e2e,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": launches * args.steps,
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -82,6 +82,9 @@ typedef struct fwi_problem {
   const float *wavelet;     /* host [nt] emitted pressure signal s(t_n)               */
   int32_t pairing;          /* fwi_pairing                                            */
   int32_t max_shots;        /* largest K (super-shots per call) this plan serves      */
+  int32_t sims_per_launch;  /* 0: all simulations of a phase share each launch
+                               (K shots, adjoint and TR together); 1: the plain form,
+                               one simulation per launch sequence                    */
 } fwi_problem;
 
 typedef struct fwi_plan fwi_plan;
@@ -145,6 +148,28 @@ int64_t fwi_plan_voxel_steps(const fwi_plan *plan, int32_t K, int32_t gradient);
 
 /* Number of kernel launches one call issues (for launch accounting). */
 int64_t fwi_plan_launches(const fwi_plan *plan, int32_t K, int32_t gradient);
+
+/* Kernels that can be timed by the profiling hook. */
+typedef enum fwi_kernel {
+  FWI_K_ZPASS_MOMENTUM = 0, FWI_K_PLANE_MOMENTUM = 1, FWI_K_ZPASS_MASS = 2, FWI_K_PLANE_MASS = 3
+} fwi_kernel;
+
+/*
+ * Profiling hook: with enable = 1, every later launch of a kernel whose bit is
+ * set in `kernel_mask` (bit k = fwi_kernel k) is bracketed by CUDA events on
+ * its stream; at most `capacity` launches are kept, later ones are not timed.
+ * enable = 0 stops recording and keeps the totals.  Host-side event objects
+ * only; no device memory is allocated.  Errors: FWI_EINVAL, FWI_ECUDA.
+ */
+fwi_status fwi_plan_profile(fwi_plan *plan, int32_t kernel_mask, int32_t enable, int32_t capacity);
+
+/*
+ * Synchronise and read the profile, per fwi_kernel k (arrays of 4): total device
+ * time ms[k] of the timed launches, their number launches[k], and the number of
+ * simulations they processed sims[k] (a launch over s simulations counts s).
+ * Resets the totals.
+ */
+fwi_status fwi_plan_profile_read(fwi_plan *plan, double *ms, int64_t *launches, int64_t *sims);
 
 /* Release the plan's host memory (not the workspace, which the caller owns). */
 fwi_status fwi_plan_destroy(fwi_plan *plan);

@@ -250,6 +250,13 @@ struct fwi_plan {
   size_t ws_bytes = 0;
   cudaStream_t last = nullptr;
   bool used = false;
+  // profiling hook
+  int prof_mask = 0;
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;   // pairs
+  std::vector<int> prof_kind;         // kernel of each pair
+  int prof_used = 0;
+  int64_t prof_sims[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -334,13 +341,56 @@ constexpr int kEpt = 8;   // complex values staged per thread per FFT pass
     CALL;                     \
   }
 
-void launch_step(fwi_plan* p, const StepParams& P, cudaStream_t st) {
+void prof_begin(fwi_plan* p, int kernel, cudaStream_t st, int nsims, int* slot) {
+  *slot = -1;
+  if (!p->prof_on || !((p->prof_mask >> kernel) & 1)) return;
+  if (2 * (p->prof_used + 1) > (int)p->prof_ev.size()) return;
+  *slot = p->prof_used++;
+  p->prof_kind[*slot] = kernel;
+  p->prof_sims[kernel] += nsims;
+  cudaEventRecord(p->prof_ev[2 * *slot], st);
+}
+void prof_end(fwi_plan* p, cudaStream_t st, int slot) {
+  if (slot >= 0) cudaEventRecord(p->prof_ev[2 * slot + 1], st);
+}
+
+// One time step for a batch of simulations (four launches).
+void launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) {
   const dim3 gz((p->mspec + kZTile - 1) / kZTile, P.nsims);
   const dim3 gp(p->prob.nz, P.nsims);
+  int slot;
+  prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
   EPT_SWITCH(p->ept_zmom, (k_zpass<0, E><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+  prof_end(p, st, slot);
+  prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
   EPT_SWITCH(p->ept_plane, (k_plane_mom<E><<<gp, kTpbPlane, p->smem_mom, st>>>(P)));
+  prof_end(p, st, slot);
+  prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
   EPT_SWITCH(p->ept_zmass, (k_zpass<1, E><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+  prof_end(p, st, slot);
+  prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
   EPT_SWITCH(p->ept_plane, (k_plane_mass<E><<<gp, kTpbPlane, p->smem_mass, st>>>(P)));
+  prof_end(p, st, slot);
+}
+
+// One time step: all simulations in one launch sequence, or (plain form) one
+// launch sequence per simulation.
+void launch_step(fwi_plan* p, const StepParams& P, cudaStream_t st) {
+  const int spl = p->prob.sims_per_launch;
+  if (spl <= 0 || spl >= P.nsims) {
+    launch_step_batch(p, P, st);
+    return;
+  }
+  for (int s0 = 0; s0 < P.nsims; s0 += spl) {
+    StepParams Q = P;
+    Q.nsims = std::min(spl, P.nsims - s0);
+    for (int i = 0; i < Q.nsims; ++i) {
+      Q.sims[i] = P.sims[s0 + i];
+      Q.tidx[i] = P.tidx[s0 + i];
+      Q.slot[i] = P.slot[s0 + i];
+    }
+    launch_step_batch(p, Q, st);
+  }
 }
 
 fwi_status zero_sim(fwi_plan* p, int s, cudaStream_t st) {
@@ -421,6 +471,7 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   if (!q.src_idx || !q.rec_idx || !q.gamma_idx || (q.n_layer > 0 && !q.layer_idx) || !q.wavelet)
     return FWI_EINVAL;
   if (q.pairing != FWI_PAIRING_LITERAL && q.pairing != FWI_PAIRING_EXACT) return FWI_EINVAL;
+  if (q.sims_per_launch < 0) return FWI_EINVAL;
   for (int a = 0; a < 3; ++a) {
     const int n = a == 0 ? q.nx : (a == 1 ? q.ny : q.nz);
     if (q.pml[a] < 0 || 2 * q.pml[a] > n) return FWI_EINVAL;
@@ -728,19 +779,65 @@ int64_t fwi_plan_voxel_steps(const fwi_plan* p, int32_t K, int32_t gradient) {
 }
 
 int64_t fwi_plan_launches(const fwi_plan* p, int32_t K, int32_t gradient) {
-  if (!p) return -1;
+  if (!p || K < 1) return -1;
   const int64_t nt = p->prob.nt, Nt = nt - 1;
-  int64_t n = 2 + 1 + 4 * nt;                       // prepare x2, source amp, steps
+  const int spl = p->prob.sims_per_launch;
+  auto seqs = [&](int nsims) -> int64_t { return (spl <= 0 || spl >= nsims) ? 1 : (nsims + spl - 1) / spl; };
+  int64_t n = 2 + 1 + 4 * nt * seqs(K);                 // prepare x2, source amplitudes, steps
   if (gradient) {
     const bool exact = p->prob.pairing == FWI_PAIRING_EXACT;
     const int64_t nit = exact ? Nt + 1 : Nt - 1;
-    n += 2 + 1 + 4 + nit * 5 + 1;                   // misfit x2, tr init, lead step, loop, final
+    n += 2 + 1 + 4 * seqs(K);                           // misfit x2, TR init, lead TR step
+    const int64_t full = std::min<int64_t>(nit, Nt - 1);  // iterations with a TR step
+    n += full * (4 * seqs(2 * K) + 1) + (nit - full) * (4 * seqs(K) + 1);
+    n += 1;                                             // gradient scatter
   }
-  (void)K;
   return n;
 }
 
+fwi_status fwi_plan_profile(fwi_plan* p, int32_t kernel_mask, int32_t enable, int32_t capacity) {
+  if (!p || kernel_mask < 0 || kernel_mask > 15 || capacity < 0) return FWI_EINVAL;
+  if (!enable) {
+    p->prof_on = false;
+    return FWI_OK;
+  }
+  if ((int)p->prof_ev.size() < 2 * capacity) {
+    for (int i = (int)p->prof_ev.size(); i < 2 * capacity; ++i) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      p->prof_ev.push_back(e);
+    }
+    p->prof_kind.resize(capacity);
+  }
+  p->prof_mask = kernel_mask;
+  p->prof_used = 0;
+  for (int k = 0; k < 4; ++k) p->prof_sims[k] = 0;
+  p->prof_on = true;
+  return FWI_OK;
+}
+
+fwi_status fwi_plan_profile_read(fwi_plan* p, double* ms, int64_t* launches, int64_t* sims) {
+  if (!p || !ms || !launches || !sims) return FWI_EINVAL;
+  for (int k = 0; k < 4; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+    sims[k] = p->prof_sims[k];
+    p->prof_sims[k] = 0;
+  }
+  if (p->prof_used > 0) CK(cudaEventSynchronize(p->prof_ev[2 * p->prof_used - 1]));
+  for (int i = 0; i < p->prof_used; ++i) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, p->prof_ev[2 * i], p->prof_ev[2 * i + 1]));
+    ms[p->prof_kind[i]] += t;
+    launches[p->prof_kind[i]] += 1;
+  }
+  p->prof_used = 0;
+  return FWI_OK;
+}
+
 fwi_status fwi_plan_destroy(fwi_plan* p) {
+  if (p)
+    for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   delete p;
   return FWI_OK;
 }

@@ -29,8 +29,10 @@ FWI_ENOTSUP = 7
 PAIRING = {"literal": 0, "exact": 1}
 
 C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_gradient",
-             "fwi_plan_status", "fwi_plan_voxel_steps", "fwi_plan_launches", "fwi_plan_destroy",
-             "fwi_status_string")
+             "fwi_plan_status", "fwi_plan_voxel_steps", "fwi_plan_launches", "fwi_plan_profile",
+             "fwi_plan_profile_read", "fwi_plan_destroy", "fwi_status_string")
+
+KERNELS = {"zpass_momentum": 0, "plane_momentum": 1, "zpass_mass": 2, "plane_mass": 3}
 
 
 class FwiError(RuntimeError):
@@ -51,6 +53,7 @@ class fwi_problem(ctypes.Structure):
         ("layer_idx", ctypes.POINTER(ctypes.c_int32)), ("gamma_idx", ctypes.POINTER(ctypes.c_int32)),
         ("wavelet", ctypes.POINTER(ctypes.c_float)),
         ("pairing", ctypes.c_int32), ("max_shots", ctypes.c_int32),
+        ("sims_per_launch", ctypes.c_int32),
     ]
 
 
@@ -79,6 +82,11 @@ def lib():
         L.fwi_plan_voxel_steps.restype = i64
         L.fwi_plan_launches.argtypes = [vp, i32, i32]
         L.fwi_plan_launches.restype = i64
+        L.fwi_plan_profile.argtypes = [vp, i32, i32, i32]
+        L.fwi_plan_profile.restype = ctypes.c_int
+        L.fwi_plan_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                            ctypes.POINTER(i64)]  # arrays of 4
+        L.fwi_plan_profile_read.restype = ctypes.c_int
         L.fwi_plan_destroy.argtypes = [vp]
         L.fwi_plan_destroy.restype = ctypes.c_int
         L.fwi_status_string.argtypes = [ctypes.c_int]
@@ -125,6 +133,18 @@ def fwi_plan_launches(plan, K, gradient) -> int:
     return lib().fwi_plan_launches(plan, K, gradient)
 
 
+def fwi_plan_profile(plan, kernel, enable, capacity) -> int:
+    return lib().fwi_plan_profile(plan, kernel, enable, capacity)
+
+
+def fwi_plan_profile_read(plan):
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    s = (ctypes.c_int64 * 4)()
+    st = lib().fwi_plan_profile_read(plan, ms, n, s)
+    return st, list(ms), list(n), list(s)
+
+
 def fwi_plan_destroy(plan) -> int:
     return lib().fwi_plan_destroy(plan)
 
@@ -160,7 +180,7 @@ class Plan:
 
     def __init__(self, *, nx, ny, nz, pml, dx, dt, c_ref, rho0, pml_alpha, nt, src_idx, rec_idx,
                  layer_idx, gamma_idx, wavelet, pairing="literal", max_shots=1, c_rec=0.0,
-                 device="cuda", workspace=None):
+                 sims_per_launch=0, device="cuda", workspace=None):
         import numpy as np
         self._keep = [_i32(src_idx), _i32(rec_idx), _i32(layer_idx), _i32(gamma_idx),
                       np.ascontiguousarray(wavelet, dtype=np.float32)]
@@ -178,6 +198,7 @@ class Plan:
         P.wavelet = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         P.pairing = PAIRING[pairing] if isinstance(pairing, str) else int(pairing)
         P.max_shots = max_shots
+        P.sims_per_launch = sims_per_launch
         self.prob = P
         st, plan, nbytes = fwi_plan_create(P)
         _check(st, "fwi_plan_create")
@@ -237,6 +258,22 @@ class Plan:
 
     def status(self) -> int:
         return fwi_plan_status(self.handle)
+
+    def profile(self, kernels=("zpass_momentum", "plane_momentum", "zpass_mass", "plane_mass"),
+                enable=True, capacity=65536):
+        """Time every launch of the named kernels with CUDA events (see fwi_plan_profile)."""
+        if isinstance(kernels, str):
+            kernels = (kernels,)
+        mask = 0
+        for k in kernels:
+            mask |= 1 << KERNELS[k]
+        _check(fwi_plan_profile(self.handle, mask, 1 if enable else 0, capacity), "fwi_plan_profile")
+
+    def profile_read(self):
+        """{kernel: (total ms, launches, simulations processed)} since profiling was enabled."""
+        st, ms, n, sims = fwi_plan_profile_read(self.handle)
+        _check(st, "fwi_plan_profile_read")
+        return {k: (ms[i], n[i], sims[i]) for k, i in KERNELS.items()}
 
     def voxel_steps(self, K, gradient=True) -> int:
         return fwi_plan_voxel_steps(self.handle, K, 1 if gradient else 0)

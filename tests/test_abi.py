@@ -50,7 +50,7 @@ def _problem(wl, **over):
     ip = ctypes.POINTER(ctypes.c_int32)
     P.src_idx, P.rec_idx, P.layer_idx, P.gamma_idx = [k.ctypes.data_as(ip) for k in keep]
     P.wavelet = wav.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
-    P.pairing, P.max_shots = 0, 2
+    P.pairing, P.max_shots, P.sims_per_launch = 0, 2, 0
     for k, v in over.items():
         setattr(P, k, v)
     return P, (keep, wav)
