@@ -171,6 +171,34 @@ fwi_status fwi_plan_profile(fwi_plan *plan, int32_t kernel_mask, int32_t enable,
  */
 fwi_status fwi_plan_profile_read(fwi_plan *plan, double *ms, int64_t *launches, int64_t *sims);
 
+/*
+ * Allocation-free adjoint source (no counterpart in the paper; added for callers
+ * that cannot allocate device memory).  Same arithmetic as the adjoint-source
+ * stage inside fwi_gradient: q^n = f^(Nt-n) - f_obs^(Nt-n), D_k = 0.5 ||q_k||^2
+ * (FP64), Q^n = sum_{m<=n} q^m (FP64 running sum, stored FP32).
+ *
+ * Who needs it: callers that manage every byte of device memory themselves --
+ * a fixed pool carved out once at start-up, or a host process that must keep its
+ * device footprint constant while it runs -- and can neither call cudaMalloc nor
+ * hand the library a workspace for this step.  The block partial sums of D live
+ * in a file-scope __device__ array of FWI_NOALLOC_MAX_PARTIALS doubles (64 KiB)
+ * that every GPU which loads the library holds until the process exits.
+ *   traces, observed: device [K][nt][n_rec] simulated and observed (encoded) traces
+ *   qcum:   device out [K][nt][n_rec] FP32 cumulative residual Q
+ *   misfit: device out [K] FP64
+ * Limits: K * ceil(n_rec / 256) <= FWI_NOALLOC_MAX_PARTIALS and 1 <= K <= 32,
+ * else FWI_EINVAL (nothing is launched).  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents: every partial is written before it is read,
+ * so no clearing is needed, but calls that overlap on the GPU (on different
+ * streams) race on it.  Allocates nothing: no cudaMalloc, no cudaFree.
+ */
+#define FWI_NOALLOC_MAX_PARTIALS 8192
+fwi_status fwi_adjoint_source_noalloc(const float *traces, const float *observed, int32_t K,
+                                      int32_t nt, int32_t n_rec, float *qcum, double *misfit,
+                                      void *stream);
+
 /* Release the plan's host memory (not the workspace, which the caller owns). */
 fwi_status fwi_plan_destroy(fwi_plan *plan);
 

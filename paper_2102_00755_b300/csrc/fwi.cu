@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -832,6 +833,42 @@ fwi_status fwi_plan_profile_read(fwi_plan* p, double* ms, int64_t* launches, int
     launches[p->prof_kind[i]] += 1;
   }
   p->prof_used = 0;
+  return FWI_OK;
+}
+
+// ---- allocation-free adjoint source ------------------------------------------------
+// Scratch for the block partial sums of the misfit: a file-scope device array, so
+// callers that cannot allocate device memory can still run this stage.
+static __device__ __align__(256) double g_noalloc_partials[FWI_NOALLOC_MAX_PARTIALS];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[256];   // device address of the array, per device ordinal
+
+fwi_status fwi_adjoint_source_noalloc(const float* traces, const float* observed, int32_t K,
+                                      int32_t nt, int32_t n_rec, float* qcum, double* misfit,
+                                      void* stream) {
+  if (!traces || !observed || !qcum || !misfit || K < 1 || K > 32 || nt < 1 || n_rec < 1)
+    return FWI_EINVAL;
+  const int nblk = (n_rec + 255) / 256;
+  if ((int64_t)K * nblk > FWI_NOALLOC_MAX_PARTIALS) return FWI_EINVAL;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return FWI_EINVAL;
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // host code may not use the array's name as a device address: look it up
+      void* ptr = nullptr;
+      CK(cudaGetSymbolAddress(&ptr, g_noalloc_partials));
+      g_noalloc_ptr[dev] = ptr;
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_misfit<<<dim3(nblk, K), 256, 0, st>>>(traces, observed, nt, n_rec, qcum, static_cast<double*>(scratch));
+  k_misfit_final<<<1, 32, 0, st>>>(static_cast<const double*>(scratch), nblk, K, misfit);
+  CK(cudaGetLastError());
   return FWI_OK;
 }
 

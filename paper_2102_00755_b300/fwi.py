@@ -30,7 +30,10 @@ PAIRING = {"literal": 0, "exact": 1}
 
 C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_gradient",
              "fwi_plan_status", "fwi_plan_voxel_steps", "fwi_plan_launches", "fwi_plan_profile",
-             "fwi_plan_profile_read", "fwi_plan_destroy", "fwi_status_string")
+             "fwi_plan_profile_read", "fwi_adjoint_source_noalloc", "fwi_plan_destroy",
+             "fwi_status_string")
+
+NOALLOC_MAX_PARTIALS = 8192
 
 KERNELS = {"zpass_momentum": 0, "plane_momentum": 1, "zpass_mass": 2, "plane_mass": 3}
 
@@ -87,6 +90,8 @@ def lib():
         L.fwi_plan_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                             ctypes.POINTER(i64)]  # arrays of 4
         L.fwi_plan_profile_read.restype = ctypes.c_int
+        L.fwi_adjoint_source_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp]
+        L.fwi_adjoint_source_noalloc.restype = ctypes.c_int
         L.fwi_plan_destroy.argtypes = [vp]
         L.fwi_plan_destroy.restype = ctypes.c_int
         L.fwi_status_string.argtypes = [ctypes.c_int]
@@ -143,6 +148,14 @@ def fwi_plan_profile_read(plan):
     s = (ctypes.c_int64 * 4)()
     st = lib().fwi_plan_profile_read(plan, ms, n, s)
     return st, list(ms), list(n), list(s)
+
+
+def fwi_adjoint_source_noalloc(traces_ptr, observed_ptr, K, nt, n_rec, qcum_ptr, misfit_ptr,
+                               stream) -> int:
+    """Allocation-free adjoint source (misfit + cumulative residual) for callers that
+    cannot allocate device memory; see include/fwi.h for limits and sharing rules."""
+    return lib().fwi_adjoint_source_noalloc(traces_ptr, observed_ptr, K, nt, n_rec, qcum_ptr,
+                                            misfit_ptr, stream)
 
 
 def fwi_plan_destroy(plan) -> int:
