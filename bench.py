@@ -161,6 +161,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--nt", type=int, default=0,
+                    help="override the number of time samples (small profiling cases only)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -181,6 +183,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     wl = synth.config2()
+    if args.nt:
+        wl.nt = args.nt
+        wl.wavelet = wl.wavelet[:args.nt]
     K = wl.weights.shape[0]
     if rank > 0:   # independent estimates per GPU (Sec. 4.5): other encoding weights
         rng = np.random.default_rng(1000 + rank)
