@@ -1,15 +1,15 @@
-// Shared-memory mixed-radix (2, 3, 4, 5, 8) complex FFT on batches of lines.
+// Shared-memory mixed-radix (2, 3, 4, 5, 8) complex FFT on groups of lines.
 //
 // The k-space derivative of App. B (Eqs. 18-19) needs 3D discrete Fourier
 // transforms of real fields on grids whose sides are products of 2, 3 and 5
-// (the PML is sized so that they are, App. B).  These routines transform many
-// lines held in one CTA's shared memory with a Stockham autosort sequence of
-// radix-R passes: pass (R, Ns) reads butterfly j's inputs at j + r*N/R, applies
-// the twiddles exp(-+2 pi i r (j mod Ns) / (Ns R)), does an R-point DFT in
-// registers and writes output r to (j/Ns)*Ns*R + (j mod Ns) + r*Ns.  Every
-// thread loads all its butterflies before a barrier and stores them after it,
-// so each pass runs in place.  Twiddles come from a per-axis FP32 table
-// W[k] = exp(-2 pi i k / N) built in FP64 on the host.
+// (the PML is sized so that they are, App. B).  A warp transforms a group of
+// lines held in shared memory with a Stockham autosort sequence of radix-R
+// passes: pass (R, Ns) reads butterfly j's inputs at j + r*N/R, applies the
+// twiddles exp(-+2 pi i r (j mod Ns) / (Ns R)), does an R-point DFT in
+// registers and writes output r to (j/Ns)*Ns*R + (j mod Ns) + r*Ns.  Lines are
+// owned by one warp for the whole transform, so passes synchronise with
+// __syncwarp only.  Twiddles come from a per-axis FP32 table
+// W[k] = exp(-2 pi i k / N) built in FP64 on the host and staged in shared memory.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -125,83 +125,166 @@ struct Dft<8, INV> {
   }
 };
 
-// One Stockham pass over `nlines` lines of length N; element e of line l lives
-// at buf[l*ls + e*es].  Requires nlines * N <= EPT * blockDim.x.
-template <int R, bool INV, int EPT>
-__device__ __forceinline__ void fft_pass(float2* buf, int nlines, int ls, int es, int N, int Ns,
-                                         const float2* __restrict__ tw) {
-  constexpr int MB = (EPT + R - 1) / R;
-  const int nb = N / R;
-  const int total = nlines * nb;
-  const int T = blockDim.x;
-  const int twstep = N / (Ns * R);
+// a / d for 0 <= a < 2^22 and d >= 1, given r = 1.0f / d: (a + 1/2) / d is at least
+// 1/(2d) away from an integer and the FP32 product errs by less than that.
+__device__ __forceinline__ int fdivi(int a, float r) { return __float2int_rz(((float)a + 0.5f) * r); }
+
+// One Stockham radix-R pass, run by a single warp over `nbf` butterflies that
+// belong to nbf / nb lines (nb = N / R butterflies per line).  Element e of line
+// l lives at buf[l*ls + e*es]; `tw` is the axis' W table in shared memory.  The
+// warp loads all its butterflies before __syncwarp and stores after it, so the
+// pass runs in place.  Each lane stages at most about EPL values: requires
+// nbf <= 32 * ceil(EPL / R).  Kept out of line so that the register budgets of
+// the different radices are not summed where a kernel dispatches on R.
+template <int R, bool INV, int EPL>
+__device__ __noinline__ void warp_pass(float2* buf, int nbf, int nb, int ls, int es, int Ns,
+                                          int twstep, const float2* tw, int lane) {
+  constexpr int MB = (EPL + R - 1) / R;
+  const float rnb = 1.0f / (float)nb;
+  const float rns = 1.0f / (float)Ns;
   float2 v[MB][R];
-  int obase[MB];
+  int ob[MB];
 #pragma unroll
-  for (int b = 0; b < MB; ++b) {
-    const int idx = threadIdx.x + b * T;
-    obase[b] = -1;
-    if (idx < total) {
-      const int line = idx / nb;
-      const int j = idx - line * nb;
-      const int jm = j % Ns;
+  for (int i = 0; i < MB; ++i) {
+    const int b = lane + 32 * i;
+    ob[i] = -1;
+    if (b < nbf) {
+      const int line = fdivi(b, rnb);
+      const int j = b - line * nb;
+      const int jq = fdivi(j, rns);
+      const int jm = j - jq * Ns;
       const float2* L = buf + line * ls;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = L[(j + r * nb) * es];
+      for (int r = 0; r < R; ++r) v[i][r] = L[(j + r * nb) * es];
       if (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(&tw[r * jm * twstep]);
+          float2 w = tw[r * jm * twstep];
           if (INV) w.y = -w.y;
-          v[b][r] = cmul(v[b][r], w);
+          v[i][r] = cmul(v[i][r], w);
         }
       }
-      Dft<R, INV>::run(v[b]);
-      obase[b] = line * ls + ((j / Ns) * Ns * R + jm) * es;
+      Dft<R, INV>::run(v[i]);
+      ob[i] = line * ls + (jq * Ns * R + jm) * es;
     }
   }
-  __syncthreads();
-  const int ostride = Ns * es;
+  __syncwarp();
+  const int os = Ns * es;
 #pragma unroll
-  for (int b = 0; b < MB; ++b) {
-    if (obase[b] >= 0) {
+  for (int i = 0; i < MB; ++i) {
+    if (ob[i] >= 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[obase[b] + r * ostride] = v[b][r];
+      for (int r = 0; r < R; ++r) buf[ob[i] + r * os] = v[i][r];
     }
   }
-  __syncthreads();
+  __syncwarp();
 }
 
-// Full transform of `nlines` lines (unnormalised).  Lines are processed in
-// balanced batches of at most EPT * blockDim.x elements so that each thread
-// stages at most EPT values per pass (requires N <= EPT * blockDim.x).
-// Callers synchronise before; the routine ends with a barrier.  The axis plan
-// is taken by value: it is never read through a pointer into kernel parameters.
-template <bool INV, int EPT>
-__device__ __forceinline__ void fft_lines(float2* buf, int nlines, int ls, int es, const AxisPlan A,
-                                       const float2* __restrict__ twall) {
-  const float2* tw = twall + A.tw_off;
+// Transform `nl` lines of length A.n by one warp (unnormalised).  Requires
+// nl * A.n <= 32 * EPL.
+template <bool INV, int EPL>
+__device__ __forceinline__ void warp_fft(float2* buf, int nl, int ls, int es, const AxisPlan& A,
+                                         const float2* tw, int lane) {
   const int N = A.n;
-  const int cap = EPT * (int)blockDim.x;
-  int lpb = cap / N;
-  const int nbat = (nlines + lpb - 1) / lpb;
-  lpb = (nlines + nbat - 1) / nbat;
-  for (int l0 = 0; l0 < nlines; l0 += lpb) {
-    const int nl = min(lpb, nlines - l0);
-    float2* bb = buf + l0 * ls;
-    int Ns = 1;
-    for (int s = 0; s < A.nstages; ++s) {
-      const int R = A.radix[s];
-      switch (R) {
-        case 2: fft_pass<2, INV, EPT>(bb, nl, ls, es, N, Ns, tw); break;
-        case 3: fft_pass<3, INV, EPT>(bb, nl, ls, es, N, Ns, tw); break;
-        case 4: fft_pass<4, INV, EPT>(bb, nl, ls, es, N, Ns, tw); break;
-        case 5: fft_pass<5, INV, EPT>(bb, nl, ls, es, N, Ns, tw); break;
-        default: fft_pass<8, INV, EPT>(bb, nl, ls, es, N, Ns, tw); break;
+  int Ns = 1;
+#pragma unroll 1
+  for (int s = 0; s < A.nstages; ++s) {
+    const int R = A.radix[s];
+    const int nb = N / R;
+    const int tws = N / (Ns * R);
+    switch (R) {
+      case 2: warp_pass<2, INV, EPL>(buf, nl * nb, nb, ls, es, Ns, tws, tw, lane); break;
+      case 3: warp_pass<3, INV, EPL>(buf, nl * nb, nb, ls, es, Ns, tws, tw, lane); break;
+      case 4: warp_pass<4, INV, EPL>(buf, nl * nb, nb, ls, es, Ns, tws, tw, lane); break;
+      case 5: warp_pass<5, INV, EPL>(buf, nl * nb, nb, ls, es, Ns, tws, tw, lane); break;
+      default: warp_pass<8, INV, EPL>(buf, nl * nb, nb, ls, es, Ns, tws, tw, lane); break;
+    }
+    Ns *= R;
+  }
+}
+
+// Lines per warp group for an axis of length n (nl * n <= 32 * EPL).
+template <int EPL>
+__host__ __device__ __forceinline__ int lines_per_group(int n) { return n >= 32 * EPL ? 1 : 32 * EPL / n; }
+
+
+// ---------------------------------------------------------------------------
+// Compile-time specialised line transforms for the common lengths: the radix
+// schedule, divisors, group sizes and loop bounds are constants, everything is
+// inlined.  LF = true maps consecutive lanes to consecutive lines (used when the
+// lines are adjacent columns, so lanes touch adjacent words).
+
+template <int M>
+struct FirstRadix {
+  static constexpr int value = (M % 8 == 0) ? 8 : (M % 4 == 0) ? 4 : (M % 2 == 0) ? 2 : (M % 3 == 0) ? 3 : 5;
+};
+
+template <int N, int R, int NS, bool INV, int G, bool LF>
+__device__ __forceinline__ void ct_pass(float2* buf, int ls, int es, const float2* tw, int lane) {
+  constexpr int NB = N / R;
+  constexpr int TOT = G * NB;
+  constexpr int MB = (TOT + 31) / 32;
+  constexpr int TWS = N / (NS * R);
+  float2 v[MB][R];
+  int ob[MB];
+#pragma unroll
+  for (int i = 0; i < MB; ++i) {
+    const int b = lane + 32 * i;
+    ob[i] = -1;
+    if (TOT % 32 == 0 || b < TOT) {
+      const int line = LF ? b % G : b / NB;
+      const int j = LF ? b / G : b % NB;
+      const int jm = j % NS;
+      const int jq = j / NS;
+      const float2* L = buf + line * ls;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = L[(j + r * NB) * es];
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[r * jm * TWS];
+          if (INV) w.y = -w.y;
+          v[i][r] = cmul(v[i][r], w);
+        }
       }
-      Ns *= R;
+      Dft<R, INV>::run(v[i]);
+      ob[i] = line * ls + (jq * NS * R + jm) * es;
     }
   }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < MB; ++i) {
+    if (ob[i] >= 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[ob[i] + r * NS * es] = v[i][r];
+    }
+  }
+  __syncwarp();
+}
+
+template <int N, int M, int NS, bool INV, int G, bool LF>
+__device__ __forceinline__ void ct_fft_rec(float2* buf, int ls, int es, const float2* tw, int lane) {
+  if constexpr (M > 1) {
+    constexpr int R = FirstRadix<M>::value;
+    static_assert(M % R == 0, "length must be a product of 2, 3 and 5");
+    ct_pass<N, R, NS, INV, G, LF>(buf, ls, es, tw, lane);
+    ct_fft_rec<N, M / R, NS * R, INV, G, LF>(buf, ls, es, tw, lane);
+  }
+}
+
+// G lines of length N by one warp (all G lines present).
+template <int N, bool INV, int G, bool LF>
+__device__ __forceinline__ void ct_fft(float2* buf, int ls, int es, const float2* tw, int lane) {
+  ct_fft_rec<N, N, 1, INV, G, LF>(buf, ls, es, tw, lane);
+}
+
+// nl <= G lines: full groups take the specialised path, a partial group the
+// runtime one (same arithmetic).
+template <int N, bool INV, int G, bool LF>
+__device__ __forceinline__ void ct_fft_n(float2* buf, int nl, int ls, int es, const AxisPlan& A,
+                                         const float2* tw, int lane) {
+  if (nl == G) ct_fft<N, INV, G, LF>(buf, ls, es, tw, lane);
+  else warp_fft<INV, 16>(buf, nl, ls, es, A, tw, lane);
 }
 
 }  // namespace fwi

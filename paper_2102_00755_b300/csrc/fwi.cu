@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -177,38 +178,64 @@ double pml_value(int i, int n, int P, double alpha, double c_ref, double dx, dou
   return std::exp(-sigma * dt / 2.0);
 }
 
+// Sparse voxel lists grouped by pair line: key = z * npair + y / 2.  `pf` is the
+// float offset of the voxel in the plane buffer seen as pair lines of 2 hx complex
+// values: 4 hx (y/2) + 2x + (y & 1).
 struct Csr {
-  std::vector<int> ptr;   // [nz+1]
-  std::vector<int> off;   // plane offset of each entry
+  std::vector<int> ptr;   // [nz*npair + 1]
   std::vector<int> vox;   // linear voxel of each entry
-  std::vector<int> mptr;  // members per entry
+  std::vector<int> pf;    // offset inside the pair line
+  std::vector<int> mptr;  // members per entry (unique lists)
   std::vector<int> mem;   // member ids
 };
 
-// unique voxels sorted by (z, offset), with the list of ids mapping to each
-Csr build_unique(const int32_t* idx, int n, int nz, int plane) {
+struct KeyGeom {
+  int nx, ny, nz, npair, hx;
+  int key(int v) const {
+    const int plane = nx * ny;
+    const int z = v / plane, r = v - z * plane, y = r / nx;
+    return z * npair + y / 2;
+  }
+  int pf(int v) const {
+    const int r = v % (nx * ny), y = r / nx, x = r - y * nx;
+    return 4 * hx * (y / 2) + 2 * x + (y & 1);
+  }
+};
+
+void finish_ptr(std::vector<int>& ptr) {
+  for (size_t k = 1; k < ptr.size(); ++k) ptr[k] += ptr[k - 1];
+}
+
+// unique voxels in increasing order, with the ids that map to each
+Csr build_unique(const int32_t* idx, int n, const KeyGeom& g) {
   std::map<int, std::vector<int>> by;
   for (int i = 0; i < n; ++i) by[idx[i]].push_back(i);
   Csr c;
-  c.ptr.assign(nz + 1, 0);
+  c.ptr.assign((size_t)g.nz * g.npair + 1, 0);
   c.mptr.push_back(0);
   for (auto& kv : by) {
-    const int z = kv.first / plane;
-    c.ptr[z + 1]++;
-    c.off.push_back(kv.first - z * plane);
+    c.ptr[g.key(kv.first) + 1]++;
     c.vox.push_back(kv.first);
+    c.pf.push_back(g.pf(kv.first));
     for (int m : kv.second) c.mem.push_back(m);
     c.mptr.push_back((int)c.mem.size());
   }
-  for (int z = 0; z < nz; ++z) c.ptr[z + 1] += c.ptr[z];
+  finish_ptr(c.ptr);
   return c;
 }
 
-std::vector<int> plane_ranges(const int32_t* sorted, int n, int nz, int plane) {
-  std::vector<int> ptr(nz + 1, 0);
-  for (int i = 0; i < n; ++i) ptr[sorted[i] / plane + 1]++;
-  for (int z = 0; z < nz; ++z) ptr[z + 1] += ptr[z];
-  return ptr;
+// all entries of an (index, id) list sorted by index
+Csr build_sorted(const std::vector<std::pair<int, int>>& e, const KeyGeom& g) {
+  Csr c;
+  c.ptr.assign((size_t)g.nz * g.npair + 1, 0);
+  for (auto& v : e) {
+    c.ptr[g.key(v.first) + 1]++;
+    c.vox.push_back(v.first);
+    c.pf.push_back(g.pf(v.first));
+    c.mem.push_back(v.second);
+  }
+  finish_ptr(c.ptr);
+  return c;
 }
 
 struct Layout {
@@ -226,23 +253,26 @@ struct Layout {
 struct fwi_plan {
   fwi_problem prob;     // scalars (pointers cleared)
   int K;                // max shots
-  int hx, npair, nxp, hxp, mspec, plane;
+  int hx, npair, mspec, plane;
   int64_t nvox;
   AxisPlan ax, ay, az;
-  int ept_plane, ept_zmom, ept_zmass;
-  size_t smem_mom, smem_mass, smem_zmom, smem_zmass;
+  size_t smem_plane, smem_zmom, smem_zmass;
+  int epl;   // values staged per lane in the runtime warp FFT passes (8 or 16)
+  int fxy;   // specialised plane side (0: runtime schedules)
+  int fz;    // specialised z length (0: runtime schedules)
+  int tz;    // z-pass tile width (columns)
   // host tables
   std::vector<float2> tw, ap[3], am[3];
   std::vector<float> kx2, ky2, kz2, lam[3], lams[3], wavelet;
-  Csr us, ur, rr;
-  std::vector<int> lay_ptr, gam_ptr, lay_idx, gam_idx;
+  Csr us, ur, rr, lay, gam;
   int n_us, n_ur;
   // workspace offsets
   Layout L;
   size_t o_tw, o_kx2, o_ky2, o_kz2, o_ap[3], o_am[3], o_lam[3], o_lams[3];
-  size_t o_us_ptr, o_us_off, o_us_vox, o_us_mptr, o_us_mem;
-  size_t o_ur_ptr, o_ur_off, o_ur_vox, o_ur_mptr, o_ur_mem;
-  size_t o_rr_ptr, o_rr_off, o_rr_col, o_lay_ptr, o_lay_idx, o_gam_ptr, o_gam_idx, o_wav;
+  size_t o_us_ptr, o_us_pf, o_us_vox, o_us_mptr, o_us_mem;
+  size_t o_ur_ptr, o_ur_pf, o_ur_vox, o_ur_mptr, o_ur_mem;
+  size_t o_rr_ptr, o_rr_pf, o_rr_col, o_lay_ptr, o_lay_vox, o_lay_pf, o_gam_ptr, o_gam_vox, o_gam_pf;
+  size_t o_wav;
   size_t o_bad, o_c2, o_us_coef, o_ur_coef, o_coefG, o_inv3c2, o_amp, o_traces, o_obs, o_qf,
       o_ghist, o_ring, o_pa, o_acc, o_dpart;
   size_t o_sims, sim_bytes, sim_field, sim_spec;
@@ -280,7 +310,7 @@ void base_params(fwi_plan* p, StepParams* P) {
   std::memset(P, 0, sizeof(*P));
   const fwi_problem& q = p->prob;
   P->nx = q.nx; P->ny = q.ny; P->nz = q.nz;
-  P->hx = p->hx; P->npair = p->npair; P->nxp = p->nxp; P->hxp = p->hxp;
+  P->hx = p->hx; P->npair = p->npair;
   P->nvox = p->nvox; P->plane = p->plane; P->mspec = p->mspec; P->nt = q.nt;
   P->n_rec = q.n_rec; P->n_layer = q.n_layer; P->n_gamma = q.n_gamma;
   P->n_us = p->n_us; P->n_ur = p->n_ur;
@@ -299,19 +329,22 @@ void base_params(fwi_plan* p, StepParams* P) {
   P->dt_rho0 = (float)(q.dt * q.rho0);
   P->c2 = at<float>(p, p->o_c2);
   P->bad = at<int>(p, p->o_bad);
-  P->us_ptr = at<int>(p, p->o_us_ptr); P->us_off = at<int>(p, p->o_us_off);
+  P->us_ptr = at<int>(p, p->o_us_ptr); P->us_vox = at<int>(p, p->o_us_vox);
+  P->us_pf = at<int>(p, p->o_us_pf);
   P->amp_src = at<float>(p, p->o_amp);
-  P->ur_ptr = at<int>(p, p->o_ur_ptr); P->ur_off = at<int>(p, p->o_ur_off);
+  P->ur_ptr = at<int>(p, p->o_ur_ptr); P->ur_vox = at<int>(p, p->o_ur_vox);
+  P->ur_pf = at<int>(p, p->o_ur_pf);
   P->ur_mptr = at<int>(p, p->o_ur_mptr); P->ur_mem = at<int>(p, p->o_ur_mem);
   P->ur_coef = at<float>(p, p->o_ur_coef);
   P->qf = at<float>(p, p->o_qf);
-  P->rr_ptr = at<int>(p, p->o_rr_ptr); P->rr_off = at<int>(p, p->o_rr_off);
+  P->rr_ptr = at<int>(p, p->o_rr_ptr); P->rr_pf = at<int>(p, p->o_rr_pf);
   P->rr_col = at<int>(p, p->o_rr_col);
   P->traces = at<float>(p, p->o_traces);
-  P->lay_ptr = at<int>(p, p->o_lay_ptr); P->lay_idx = at<int>(p, p->o_lay_idx);
+  P->lay_ptr = at<int>(p, p->o_lay_ptr); P->lay_vox = at<int>(p, p->o_lay_vox);
+  P->lay_pf = at<int>(p, p->o_lay_pf);
   P->ghist = at<float>(p, p->o_ghist);
   P->inv3c2 = at<float>(p, p->o_inv3c2);
-  P->gam_ptr = at<int>(p, p->o_gam_ptr); P->gam_idx = at<int>(p, p->o_gam_idx);
+  P->gam_ptr = at<int>(p, p->o_gam_ptr); P->gam_pf = at<int>(p, p->o_gam_pf);
   P->pa = at<float>(p, p->o_pa);
   P->ring = at<float>(p, p->o_ring);
 }
@@ -322,25 +355,49 @@ void base_params(fwi_plan* p, StepParams* P) {
     if (e_ != cudaSuccess) return FWI_ECUDA;    \
   } while (0)
 
-template <int EPT>
-void set_attrs_plane(fwi_plan* p) {
-  cudaFuncSetAttribute(k_plane_mom<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_mom);
-  cudaFuncSetAttribute(k_plane_mass<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_mass);
-  cudaFuncSetAttribute(k_tr_init<EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_mom);
-}
-template <int EPT>
-void set_attrs_z(fwi_plan* p) {
-  cudaFuncSetAttribute(k_zpass<0, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmom);
-  cudaFuncSetAttribute(k_zpass<1, EPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmass);
-}
-
-constexpr int kEpt = 8;   // complex values staged per thread per FFT pass
-#define EPT_SWITCH(ept, CALL) \
-  {                           \
-    constexpr int E = kEpt;   \
-    (void)(ept);              \
-    CALL;                     \
+// Kernel instantiations: specialised transforms for square planes of side FXY in
+// {32, 64, 96, 128, 160} and z lengths FZ in {32, 48, 64, 80, 96, 128}; any other
+// 2-3-5-smooth size (up to 512) takes the runtime radix schedule (F = 0) with 8
+// (axes <= 256) or 16 values staged per lane.
+#define PLANE_DISPATCH(p, CALL)                                         \
+  switch ((p)->fxy) {                                                   \
+    case 32: { constexpr int E = 8, F = 32; CALL; } break;              \
+    case 64: { constexpr int E = 8, F = 64; CALL; } break;              \
+    case 96: { constexpr int E = 8, F = 96; CALL; } break;              \
+    case 128: { constexpr int E = 8, F = 128; CALL; } break;            \
+    case 160: { constexpr int E = 8, F = 160; CALL; } break;            \
+    default:                                                            \
+      if ((p)->epl == 8) { constexpr int E = 8, F = 0; CALL; }          \
+      else { constexpr int E = 16, F = 0; CALL; }                       \
   }
+#define Z_DISPATCH(p, CALL)                                             \
+  switch ((p)->fz) {                                                    \
+    case 32: { constexpr int E = 8, FZ = 32; CALL; } break;             \
+    case 48: { constexpr int E = 8, FZ = 48; CALL; } break;             \
+    case 64: { constexpr int E = 8, FZ = 64; CALL; } break;             \
+    case 80: { constexpr int E = 8, FZ = 80; CALL; } break;             \
+    case 96: { constexpr int E = 8, FZ = 96; CALL; } break;             \
+    case 128: { constexpr int E = 8, FZ = 128; CALL; } break;           \
+    default:                                                            \
+      if ((p)->epl == 8) { constexpr int E = 8, FZ = 0; CALL; }         \
+      else { constexpr int E = 16, FZ = 0; CALL; }                      \
+  }
+
+template <int E, int F>
+void set_attrs_plane(fwi_plan* p) {
+  cudaFuncSetAttribute(k_plane_mom<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_plane);
+  cudaFuncSetAttribute(k_plane_mass<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_plane);
+  cudaFuncSetAttribute(k_tr_init<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_plane);
+}
+template <int E, int FZ>
+void set_attrs_z(fwi_plan* p) {
+  cudaFuncSetAttribute(k_zpass<0, E, FZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmom);
+  cudaFuncSetAttribute(k_zpass<1, E, FZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmass);
+}
+void set_attrs(fwi_plan* p) {
+  PLANE_DISPATCH(p, (set_attrs_plane<E, F>(p)));
+  Z_DISPATCH(p, (set_attrs_z<E, FZ>(p)));
+}
 
 void prof_begin(fwi_plan* p, int kernel, cudaStream_t st, int nsims, int* slot) {
   *slot = -1;
@@ -357,20 +414,20 @@ void prof_end(fwi_plan* p, cudaStream_t st, int slot) {
 
 // One time step for a batch of simulations (four launches).
 void launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) {
-  const dim3 gz((p->mspec + kZTile - 1) / kZTile, P.nsims);
+  const dim3 gz((p->mspec + p->tz - 1) / p->tz, P.nsims);
   const dim3 gp(p->prob.nz, P.nsims);
   int slot;
   prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
-  EPT_SWITCH(p->ept_zmom, (k_zpass<0, E><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+  Z_DISPATCH(p, (k_zpass<0, E, FZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
-  EPT_SWITCH(p->ept_plane, (k_plane_mom<E><<<gp, kTpbPlane, p->smem_mom, st>>>(P)));
+  PLANE_DISPATCH(p, (k_plane_mom<E, F, F><<<gp, kTpbPlane, p->smem_plane, st>>>(P)));
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
-  EPT_SWITCH(p->ept_zmass, (k_zpass<1, E><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+  Z_DISPATCH(p, (k_zpass<1, E, FZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
-  EPT_SWITCH(p->ept_plane, (k_plane_mass<E><<<gp, kTpbPlane, p->smem_mass, st>>>(P)));
+  PLANE_DISPATCH(p, (k_plane_mass<E, F, F><<<gp, kTpbPlane, p->smem_plane, st>>>(P)));
   prof_end(p, st, slot);
 }
 
@@ -406,8 +463,8 @@ fwi_status prepare(fwi_plan* p, const float* c, cudaStream_t st) {
   k_prepare_c<<<592, 256, 0, st>>>(c, at<float>(p, p->o_c2), p->nvox, (float)q.c_ref, at<int>(p, p->o_bad));
   k_prepare_coefs<<<148, 256, 0, st>>>(c, q.dt, q.dx, at<int>(p, p->o_us_vox), p->n_us,
                                        at<float>(p, p->o_us_coef), at<int>(p, p->o_ur_vox), p->n_ur,
-                                       at<float>(p, p->o_ur_coef), at<int>(p, p->o_gam_idx), q.n_gamma,
-                                       at<float>(p, p->o_coefG), at<int>(p, p->o_lay_idx), q.n_layer,
+                                       at<float>(p, p->o_ur_coef), at<int>(p, p->o_gam_vox), q.n_gamma,
+                                       at<float>(p, p->o_coefG), at<int>(p, p->o_lay_vox), q.n_layer,
                                        at<float>(p, p->o_inv3c2));
   CK(cudaGetLastError());
   return FWI_OK;
@@ -503,8 +560,6 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   p->nvox = nvox;
   p->hx = q.nx / 2 + 1;
   p->npair = (q.ny + 1) / 2;
-  p->nxp = q.nx;
-  p->hxp = p->hx;
   p->plane = q.nx * q.ny;
   p->mspec = p->hx * q.ny;
   if (!factor235(q.nx, &p->ax) || !factor235(q.ny, &p->ay) || !factor235(q.nz, &p->az)) {
@@ -540,37 +595,46 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
     }
   }
   p->wavelet.assign(prob->wavelet, prob->wavelet + q.nt);
-  p->us = build_unique(prob->src_idx, q.n_src, q.nz, p->plane);
-  p->ur = build_unique(prob->rec_idx, q.n_rec, q.nz, p->plane);
-  p->n_us = (int)p->us.off.size();
-  p->n_ur = (int)p->ur.off.size();
-  // receivers to record, grouped by plane, keeping their column
+  const KeyGeom kg{q.nx, q.ny, q.nz, p->npair, p->hx};
+  p->us = build_unique(prob->src_idx, q.n_src, kg);
+  p->ur = build_unique(prob->rec_idx, q.n_rec, kg);
+  p->n_us = (int)p->us.vox.size();
+  p->n_ur = (int)p->ur.vox.size();
   {
     std::vector<std::pair<int, int>> e;
     for (int r = 0; r < q.n_rec; ++r) e.push_back({prob->rec_idx[r], r});
     std::stable_sort(e.begin(), e.end());
-    p->rr.ptr.assign(q.nz + 1, 0);
-    for (auto& v : e) {
-      const int z = v.first / p->plane;
-      p->rr.ptr[z + 1]++;
-      p->rr.off.push_back(v.first - z * p->plane);
-      p->rr.mem.push_back(v.second);
-    }
-    for (int z = 0; z < q.nz; ++z) p->rr.ptr[z + 1] += p->rr.ptr[z];
+    p->rr = build_sorted(e, kg);                 // receivers to record, with their column
+    e.clear();
+    for (int j = 0; j < q.n_layer; ++j) e.push_back({prob->layer_idx[j], j});
+    p->lay = build_sorted(e, kg);
+    e.clear();
+    for (int j = 0; j < q.n_gamma; ++j) e.push_back({prob->gamma_idx[j], j});
+    p->gam = build_sorted(e, kg);
   }
-  p->lay_idx.assign(prob->layer_idx, prob->layer_idx + q.n_layer);
-  p->gam_idx.assign(prob->gamma_idx, prob->gamma_idx + q.n_gamma);
-  p->lay_ptr = plane_ranges(prob->layer_idx, q.n_layer, q.nz, p->plane);
-  p->gam_ptr = plane_ranges(prob->gamma_idx, q.n_gamma, q.nz, p->plane);
 
-  // launch shapes
-  const size_t plane_elems = std::max((size_t)p->npair * p->nxp, (size_t)q.ny * p->hxp);
-  p->ept_plane = p->ept_zmom = p->ept_zmass = 8;
-  p->smem_mom = plane_elems * sizeof(float2);
-  p->smem_mass = p->smem_mom + (size_t)p->plane * sizeof(float);
-  p->smem_zmom = (size_t)2 * kZTile * q.nz * sizeof(float2);
-  p->smem_zmass = (size_t)3 * kZTile * q.nz * sizeof(float2);
-  if (std::max(q.nx, std::max(q.ny, q.nz)) > 8 * kTpbZ || p->smem_mass > 227 * 1024 ||
+  // launch shapes: every axis must fit one warp group (n <= 512)
+  p->epl = std::max(q.nx, std::max(q.ny, q.nz)) <= 256 ? 8 : 16;
+  auto in = [](int v, std::initializer_list<int> l) { for (int x : l) if (x == v) return true; return false; };
+  p->fxy = (q.nx == q.ny && in(q.nx, {32, 64, 96, 128, 160})) ? q.nx : 0;
+  p->fz = in(q.nz, {32, 48, 64, 80, 96, 128}) ? q.nz : 0;
+  p->tz = p->fz > 0 ? 32 : 16;
+  const int ntw = ((q.nx + q.ny + 31) & ~31);
+  {
+    int g;
+    if (p->fxy > 0) {
+      g = 1;
+      while (2 * g <= 256 / p->fxy) g *= 2;                      // pair lines per warp group
+    } else {
+      g = std::max(1, 16 * p->epl / p->hx);
+    }
+    const size_t stage_floats = (size_t)(kTpbPlane / 32) * 4 * 2 * g * q.nx;
+    p->smem_plane = ((size_t)ntw + (size_t)p->npair * 2 * p->hx) * sizeof(float2) + stage_floats * 4;
+  }
+  const size_t ztw = (size_t)((q.nz + 31) & ~31);
+  p->smem_zmom = (ztw + (size_t)(2 * p->tz + 4) * q.nz) * sizeof(float2);
+  p->smem_zmass = (ztw + (size_t)(3 * p->tz + 4) * q.nz) * sizeof(float2);
+  if (std::max(q.nx, std::max(q.ny, q.nz)) > 512 || p->smem_plane > 227 * 1024 ||
       p->smem_zmass > 227 * 1024) {
     delete p;
     return FWI_ENOTSUP;
@@ -587,13 +651,16 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
     p->o_lam[a] = L.add(p->lam[a].size() * 4);
     p->o_lams[a] = L.add(p->lams[a].size() * 4);
   }
-  p->o_us_ptr = L.add((q.nz + 1) * 4); p->o_us_off = L.add(p->n_us * 4); p->o_us_vox = L.add(p->n_us * 4);
+  const size_t nkey = (size_t)q.nz * p->npair + 1;
+  p->o_us_ptr = L.add(nkey * 4); p->o_us_pf = L.add(p->n_us * 4); p->o_us_vox = L.add(p->n_us * 4);
   p->o_us_mptr = L.add((p->n_us + 1) * 4); p->o_us_mem = L.add(q.n_src * 4);
-  p->o_ur_ptr = L.add((q.nz + 1) * 4); p->o_ur_off = L.add(p->n_ur * 4); p->o_ur_vox = L.add(p->n_ur * 4);
+  p->o_ur_ptr = L.add(nkey * 4); p->o_ur_pf = L.add(p->n_ur * 4); p->o_ur_vox = L.add(p->n_ur * 4);
   p->o_ur_mptr = L.add((p->n_ur + 1) * 4); p->o_ur_mem = L.add(q.n_rec * 4);
-  p->o_rr_ptr = L.add((q.nz + 1) * 4); p->o_rr_off = L.add(q.n_rec * 4); p->o_rr_col = L.add(q.n_rec * 4);
-  p->o_lay_ptr = L.add((q.nz + 1) * 4); p->o_lay_idx = L.add((size_t)q.n_layer * 4 + 4);
-  p->o_gam_ptr = L.add((q.nz + 1) * 4); p->o_gam_idx = L.add((size_t)q.n_gamma * 4);
+  p->o_rr_ptr = L.add(nkey * 4); p->o_rr_pf = L.add(q.n_rec * 4); p->o_rr_col = L.add(q.n_rec * 4);
+  p->o_lay_ptr = L.add(nkey * 4); p->o_lay_vox = L.add((size_t)q.n_layer * 4 + 4);
+  p->o_lay_pf = L.add((size_t)q.n_layer * 4 + 4);
+  p->o_gam_ptr = L.add(nkey * 4); p->o_gam_vox = L.add((size_t)q.n_gamma * 4);
+  p->o_gam_pf = L.add((size_t)q.n_gamma * 4);
   p->o_wav = L.add((size_t)nt * 4);
   p->o_bad = L.add(4);
   p->o_c2 = L.add((size_t)nvox * 4);
@@ -637,27 +704,25 @@ fwi_status fwi_plan_bind_workspace(fwi_plan* p, void* dev_ptr, size_t bytes) {
     CK(up(p->o_lam[a], p->lam[a].data(), p->lam[a].size() * 4));
     CK(up(p->o_lams[a], p->lams[a].data(), p->lams[a].size() * 4));
   }
-  CK(up(p->o_us_ptr, p->us.ptr.data(), p->us.ptr.size() * 4));
-  CK(up(p->o_us_off, p->us.off.data(), p->us.off.size() * 4));
-  CK(up(p->o_us_vox, p->us.vox.data(), p->us.vox.size() * 4));
+  auto upc = [&](const Csr& c, size_t o_ptr, size_t o_vox, size_t o_pf) -> cudaError_t {
+    cudaError_t e;
+    if ((e = up(o_ptr, c.ptr.data(), c.ptr.size() * 4)) != cudaSuccess) return e;
+    if ((e = up(o_vox, c.vox.data(), c.vox.size() * 4)) != cudaSuccess) return e;
+    return up(o_pf, c.pf.data(), c.pf.size() * 4);
+  };
+  CK(upc(p->us, p->o_us_ptr, p->o_us_vox, p->o_us_pf));
   CK(up(p->o_us_mptr, p->us.mptr.data(), p->us.mptr.size() * 4));
   CK(up(p->o_us_mem, p->us.mem.data(), p->us.mem.size() * 4));
-  CK(up(p->o_ur_ptr, p->ur.ptr.data(), p->ur.ptr.size() * 4));
-  CK(up(p->o_ur_off, p->ur.off.data(), p->ur.off.size() * 4));
-  CK(up(p->o_ur_vox, p->ur.vox.data(), p->ur.vox.size() * 4));
+  CK(upc(p->ur, p->o_ur_ptr, p->o_ur_vox, p->o_ur_pf));
   CK(up(p->o_ur_mptr, p->ur.mptr.data(), p->ur.mptr.size() * 4));
   CK(up(p->o_ur_mem, p->ur.mem.data(), p->ur.mem.size() * 4));
   CK(up(p->o_rr_ptr, p->rr.ptr.data(), p->rr.ptr.size() * 4));
-  CK(up(p->o_rr_off, p->rr.off.data(), p->rr.off.size() * 4));
+  CK(up(p->o_rr_pf, p->rr.pf.data(), p->rr.pf.size() * 4));
   CK(up(p->o_rr_col, p->rr.mem.data(), p->rr.mem.size() * 4));
-  CK(up(p->o_lay_ptr, p->lay_ptr.data(), p->lay_ptr.size() * 4));
-  CK(up(p->o_lay_idx, p->lay_idx.data(), p->lay_idx.size() * 4));
-  CK(up(p->o_gam_ptr, p->gam_ptr.data(), p->gam_ptr.size() * 4));
-  CK(up(p->o_gam_idx, p->gam_idx.data(), p->gam_idx.size() * 4));
+  CK(upc(p->lay, p->o_lay_ptr, p->o_lay_vox, p->o_lay_pf));
+  CK(upc(p->gam, p->o_gam_ptr, p->o_gam_vox, p->o_gam_pf));
   CK(up(p->o_wav, p->wavelet.data(), p->wavelet.size() * 4));
-  EPT_SWITCH(p->ept_plane, set_attrs_plane<E>(p));
-  EPT_SWITCH(p->ept_zmom, set_attrs_z<E>(p));
-  EPT_SWITCH(p->ept_zmass, set_attrs_z<E>(p));
+  set_attrs(p);
   CK(cudaGetLastError());
   return FWI_OK;
 }
@@ -717,7 +782,7 @@ fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32
     T.tidx[k] = 1;
     T.slot[k] = 1;
   }
-  EPT_SWITCH(p->ept_plane, (k_tr_init<E><<<dim3(q.nz, K), kTpbPlane, p->smem_mom, st>>>(T)));
+  PLANE_DISPATCH(p, (k_tr_init<E, F, F><<<dim3(q.nz, K), kTpbPlane, p->smem_plane, st>>>(T)));
   launch_step(p, T, st);
   // interleaved adjoint and TR iterations
   const bool exact = q.pairing == FWI_PAIRING_EXACT;
@@ -749,7 +814,7 @@ fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32
   // mean over shots, scaled to dD/dc if requested
   const double scale = q.c_rec > 0 ? q.dx * q.c_rec / 2.0 : 1.0;
   CK(cudaMemsetAsync(grad, 0, (size_t)p->nvox * 8, st));
-  k_grad_final<<<(q.n_gamma + 255) / 256, 256, 0, st>>>(at<double>(p, p->o_acc), at<int>(p, p->o_gam_idx),
+  k_grad_final<<<(q.n_gamma + 255) / 256, 256, 0, st>>>(at<double>(p, p->o_acc), at<int>(p, p->o_gam_vox),
                                                         q.n_gamma, K, scale, grad);
   if (traces)
     CK(cudaMemcpyAsync(traces, p->ws + p->o_traces, (size_t)K * nt * q.n_rec * 4,
