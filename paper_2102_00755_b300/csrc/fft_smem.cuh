@@ -278,13 +278,17 @@ __device__ __forceinline__ void ct_fft(float2* buf, int ls, int es, const float2
   ct_fft_rec<N, N, 1, INV, G, LF>(buf, ls, es, tw, lane);
 }
 
-// nl <= G lines: full groups take the specialised path, a partial group the
-// runtime one (same arithmetic).
+// nl <= G lines: a full group in one go, a partial group line by line (same
+// arithmetic, still specialised).
 template <int N, bool INV, int G, bool LF>
 __device__ __forceinline__ void ct_fft_n(float2* buf, int nl, int ls, int es, const AxisPlan& A,
                                          const float2* tw, int lane) {
-  if (nl == G) ct_fft<N, INV, G, LF>(buf, ls, es, tw, lane);
-  else warp_fft<INV, 16>(buf, nl, ls, es, A, tw, lane);
+  (void)A;
+  if (nl == G) {
+    ct_fft<N, INV, G, LF>(buf, ls, es, tw, lane);
+  } else {
+    for (int l = 0; l < nl; ++l) ct_fft<N, INV, 1, LF>(buf + l * ls, ls, es, tw, lane);
+  }
 }
 
 }  // namespace fwi

@@ -256,7 +256,7 @@ struct fwi_plan {
   int hx, npair, mspec, plane;
   int64_t nvox;
   AxisPlan ax, ay, az;
-  size_t smem_plane, smem_zmom, smem_zmass;
+  size_t smem_plane, smem_mass, smem_zmom, smem_zmass;
   int epl;   // values staged per lane in the runtime warp FFT passes (8 or 16)
   int fxy;   // specialised plane side (0: runtime schedules)
   int fz;    // specialised z length (0: runtime schedules)
@@ -386,7 +386,7 @@ void base_params(fwi_plan* p, StepParams* P) {
 template <int E, int F>
 void set_attrs_plane(fwi_plan* p) {
   cudaFuncSetAttribute(k_plane_mom<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_plane);
-  cudaFuncSetAttribute(k_plane_mass<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_plane);
+  cudaFuncSetAttribute(k_plane_mass<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_mass);
   cudaFuncSetAttribute(k_tr_init<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_plane);
 }
 template <int E, int FZ>
@@ -427,7 +427,7 @@ void launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) {
   Z_DISPATCH(p, (k_zpass<1, E, FZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
-  PLANE_DISPATCH(p, (k_plane_mass<E, F, F><<<gp, kTpbPlane, p->smem_plane, st>>>(P)));
+  PLANE_DISPATCH(p, (k_plane_mass<E, F, F><<<gp, kTpbPlane, p->smem_mass, st>>>(P)));
   prof_end(p, st, slot);
 }
 
@@ -621,20 +621,25 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   p->tz = p->fz > 0 ? 32 : 16;
   const int ntw = ((q.nx + q.ny + 31) & ~31);
   {
-    int g;
-    if (p->fxy > 0) {
-      g = 1;
-      while (2 * g <= 256 / p->fxy) g *= 2;                      // pair lines per warp group
-    } else {
-      g = std::max(1, 16 * p->epl / p->hx);
-    }
-    const size_t stage_floats = (size_t)(kTpbPlane / 32) * 4 * 2 * g * q.nx;
-    p->smem_plane = ((size_t)ntw + (size_t)p->npair * 2 * p->hx) * sizeof(float2) + stage_floats * 4;
+    // pair lines per warp group: momentum (x work budget 256) and mass (128)
+    auto group = [&](int budget) {
+      int g = 1;
+      if (p->fxy > 0) {
+        while (2 * g <= budget / p->fxy) g *= 2;
+      } else {
+        g = std::max(1, (budget / 256) * 16 * p->epl / p->hx);
+      }
+      return g;
+    };
+    const size_t base = ((size_t)ntw + (size_t)p->npair * 2 * p->hx) * sizeof(float2);
+    const size_t warps = kTpbPlane / 32;
+    p->smem_plane = base + warps * 1 * 2 * group(256) * q.nx * 4;   // one staged array
+    p->smem_mass = base + warps * 4 * 2 * group(128) * q.nx * 4;    // four staged arrays
   }
   const size_t ztw = (size_t)((q.nz + 31) & ~31);
   p->smem_zmom = (ztw + (size_t)(2 * p->tz + 4) * q.nz) * sizeof(float2);
   p->smem_zmass = (ztw + (size_t)(3 * p->tz + 4) * q.nz) * sizeof(float2);
-  if (std::max(q.nx, std::max(q.ny, q.nz)) > 512 || p->smem_plane > 227 * 1024 ||
+  if (std::max(q.nx, std::max(q.ny, q.nz)) > 512 || p->smem_mass > 227 * 1024 ||
       p->smem_zmass > 227 * 1024) {
     delete p;
     return FWI_ENOTSUP;

@@ -210,18 +210,20 @@ __device__ __forceinline__ void warp_prefetch_rows(float* stage, const float* __
 // Compile-time configuration of the plane kernels.  FX, FY > 0: specialised
 // transforms for nx = FX, ny = FY; 0: runtime radix schedules with EPL values
 // staged per lane.  GX pair lines (x work) and GY columns (y transforms) per warp
-// group; PI / UI: per-lane staging of the C2R packing / R2C unpacking.
+// group; PI / UI: per-lane staging of the C2R packing / R2C unpacking.  XW = 256
+// is the x work budget per group (pair lines * nx); the mass kernel halves it to
+// keep its four staged state arrays small.
 __host__ __device__ constexpr int pow2_floor(int v) { return v <= 1 ? 1 : 2 * pow2_floor(v / 2); }
 
-template <int EPL, int FX, int FY>
+template <int EPL, int FX, int FY, int XW = 256>
 struct PlaneCfg {
-  static constexpr int GXc = FX > 0 ? pow2_floor(256 / FX) : 0;
+  static constexpr int GXc = FX > 0 ? pow2_floor(XW / FX) : 0;
   static constexpr int GYc = FY > 0 ? pow2_floor(256 / FY) : 0;
   static constexpr int PI = FX > 0 ? (GXc * FX + 31) / 32 : EPL;
   static constexpr int UI = FX > 0 ? (GXc * (FX / 2 + 1) + 31) / 32 : EPL / 2;
   __device__ static int gx(const StepParams& P) {
     if (FX > 0) return GXc;
-    const int g = 16 * EPL / P.hx;   // group * 2 hx <= 32 EPL
+    const int g = (XW / 256) * 16 * EPL / P.hx;   // group * 2 hx <= 32 EPL
     return g < 1 ? 1 : g;
   }
   __device__ static int gy(const StepParams& P) { return FY > 0 ? GYc : lines_per_group<EPL>(P.ny); }
@@ -390,6 +392,7 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_plane_mom(const __grid_constan
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = C::gx(P);
   // component order z, x, y: R -> V_z (same buffer), Q -> V_x (spec[2]), Q -> V_y (spec[0])
+#pragma unroll 1
   for (int cc = 0; cc < 3; ++cc) {
     const int comp = cc == 0 ? 2 : cc - 1;
     const float2* src = (comp == 2 ? S.spec[1] : S.spec[0]) + soff;
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_plane_mom(const __grid_constan
 // ------------------------------------------------------------------ mass plane
 template <int EPL, int FX, int FY>
 __global__ void __launch_bounds__(kTpbPlane, 2) k_plane_mass(const __grid_constant__ StepParams P) {
-  using C = PlaneCfg<EPL, FX, FY>;
+  using C = PlaneCfg<EPL, FX, FY, 128>;
   if (*P.bad) return;
   extern __shared__ float2 sm_raw[];
   const float2* twx = sm_raw;
@@ -461,6 +464,7 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_plane_mass(const __grid_consta
   const float* rx = S.rho[0] + voff;
   const float* rz = S.rho[2] + voff;
   // component order x (spec[2]), z (spec[1]), y (spec[0]); the last one assembles p
+#pragma unroll 1
   for (int cc = 0; cc < 3; ++cc) {
     const int comp = cc == 0 ? 0 : (cc == 1 ? 2 : 1);
     const float2* src = (comp == 0 ? S.spec[2] : (comp == 2 ? S.spec[1] : S.spec[0])) + soff;
