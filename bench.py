@@ -152,6 +152,84 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args):
+    """16 encoded-gradient instances of uneven grids (4 each of 64^3, 96x96x48, 128x128x64,
+    160x160x80; 1200..2000 steps) as one captured CUDA graph, against the same instances run
+    one after another (default batching inside each instance, and the plain form)."""
+    import torch
+
+    from paper_2102_00755_b300 import fwi, synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    wls = [synth.config3_instance(i) for i in range(16)]
+    if args.nt:
+        for wl in wls:
+            wl.nt = args.nt
+            wl.wavelet = wl.wavelet[:args.nt]
+    plans, plains, cs, ws, obs = [], [], [], [], []
+    for wl in wls:
+        plan = fwi.Plan.from_workload(wl, max_shots=1, device=dev)
+        w = torch.tensor(wl.weights, dtype=torch.float32, device=dev)
+        obs.append(plan.forward(torch.tensor(wl.c_true, dtype=torch.float32, device=dev).reshape(-1), w))
+        plans.append(plan)
+        cs.append(torch.tensor(wl.c_model, dtype=torch.float32, device=dev).reshape(-1))
+        ws.append(w)
+    vsteps = sum(p.voxel_steps(1, True) for p in plans)
+    Ds = [torch.empty(1, dtype=torch.float64, device=dev) for _ in plans]
+    gs = [torch.empty(p.n_vox, dtype=torch.float64, device=dev) for p in plans]
+    batch = fwi.Batch(plans)
+    t0 = time.perf_counter()
+    batch.gradient(cs, ws, obs, misfits=Ds, grads=gs)
+    torch.cuda.synchronize(dev)
+    capture_s = time.perf_counter() - t0
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        return sum(ts) / len(ts)
+
+    for _ in range(args.warmup - 1):
+        batch.gradient(cs, ws, obs, misfits=Ds, grads=gs)
+    ms_graph = timed(lambda: batch.gradient(cs, ws, obs, misfits=Ds, grads=gs), args.steps)
+
+    def sequential():
+        for p, c, w, o, D, g in zip(plans, cs, ws, obs, Ds, gs):
+            p.gradient(c, w, o, misfit=D, grad=g)
+    sequential()
+    ms_seq = timed(sequential, 1)
+    for p in plans:
+        p.close()
+    plains = [fwi.Plan.from_workload(wl, max_shots=1, sims_per_launch=1, device=dev) for wl in wls]
+
+    def plain():
+        for p, c, w, o, D, g in zip(plains, cs, ws, obs, Ds, gs):
+            p.gradient(c, w, o, misfit=D, grad=g)
+    plain()
+    ms_plain = timed(plain, 1)
+    G = lambda ms: vsteps / (ms / 1e3) / 1e9
+    out = {"metric": METRIC, "value": G(ms_graph), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batching: 16 encoded gradients of uneven grids (4 each of 64^3, "
+                                  "96x96x48, 128x128x64, 160x160x80), 1200-2000 steps, one captured graph",
+                      "voxel_steps_per_step": vsteps, "graph_nodes": batch.nodes(),
+                      "capture_and_first_run_s": capture_s},
+           "gradients_per_h": 3600.0 * 16 / (ms_graph / 1e3),
+           "sequential": {"value": G(ms_seq), "ms_per_step": ms_seq,
+                          "gradients_per_h": 3600.0 * 16 / (ms_seq / 1e3)},
+           "plain": {"value": G(ms_plain), "ms_per_step": ms_plain,
+                     "gradients_per_h": 3600.0 * 16 / (ms_plain / 1e3),
+                     "form": "one simulation per launch sequence, instances one after another"}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,9 +241,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--nt", type=int, default=0,
                     help="override the number of time samples (small profiling cases only)")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch"],
+                    help="plain: the 128x128x64 gradient (the reported line); batch: the 16-instance "
+                         "uneven-grid configuration as one captured graph vs sequential forms")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
         return
 
     import torch

@@ -199,6 +199,27 @@ fwi_status fwi_adjoint_source_noalloc(const float *traces, const float *observed
                                       int32_t nt, int32_t n_rec, float *qcum, double *misfit,
                                       void *stream);
 
+/*
+ * Batched form: gradients of n independent problems (plans, possibly of different
+ * grid sizes, each with its own workspace) submitted as one CUDA graph launch.
+ * The first fwi_batch_gradient call with a given set of arguments captures every
+ * plan's launch sequence into one graph, one stream branch per plan, so the
+ * instances overlap on the GPU; later calls with identical arguments replay it
+ * (any change of pointer or K re-captures).  Plans must not be used elsewhere
+ * while a batch that contains them runs.  Results are identical to n separate
+ * fwi_gradient calls.  Errors: FWI_EINVAL, FWI_ECUDA.
+ */
+typedef struct fwi_batch fwi_batch;
+fwi_status fwi_batch_create(int32_t n, fwi_plan *const *plans, fwi_batch **out);
+/* Arrays of n entries, element i as in fwi_gradient for plans[i]; traces may be NULL. */
+fwi_status fwi_batch_gradient(fwi_batch *batch, const float *const *c, const float *const *weights,
+                              const int32_t *K, const float *const *observed,
+                              const int32_t *observed_encoded, double *const *misfit,
+                              double *const *grad, void *stream);
+/* Kernel launches the captured graph holds (0 before the first capture). */
+int64_t fwi_batch_nodes(const fwi_batch *batch);
+fwi_status fwi_batch_destroy(fwi_batch *batch);
+
 /* Release the plan's host memory (not the workspace, which the caller owns). */
 fwi_status fwi_plan_destroy(fwi_plan *plan);
 

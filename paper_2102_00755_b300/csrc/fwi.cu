@@ -942,6 +942,111 @@ fwi_status fwi_adjoint_source_noalloc(const float* traces, const float* observed
   return FWI_OK;
 }
 
+// ---- batched form: one captured graph over several plans --------------------------------
+struct fwi_batch {
+  std::vector<fwi_plan*> plans;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t origin = nullptr;  // capture stream (the caller's may be the legacy default)
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uintptr_t> key;     // arguments the graph was captured with
+  int64_t nodes = 0;
+};
+
+fwi_status fwi_batch_create(int32_t n, fwi_plan* const* plans, fwi_batch** out) {
+  if (n < 1 || !plans || !out) return FWI_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!plans[i] || !plans[i]->ws) return FWI_EINVAL;
+  fwi_batch* b = new (std::nothrow) fwi_batch();
+  if (!b) return FWI_ENOMEM;
+  b->plans.assign(plans, plans + n);
+  b->side.resize(n);
+  b->join.resize(n);
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    fwi_batch_destroy(b);
+    return FWI_ECUDA;
+  }
+  *out = b;
+  return FWI_OK;
+}
+
+fwi_status fwi_batch_gradient(fwi_batch* b, const float* const* c, const float* const* w, const int32_t* K,
+                              const float* const* observed, const int32_t* observed_encoded,
+                              double* const* misfit, double* const* grad, void* stream) {
+  if (!b || !c || !w || !K || !observed || !observed_encoded || !misfit || !grad) return FWI_EINVAL;
+  const int n = (int)b->plans.size();
+  std::vector<uintptr_t> key;
+  for (int i = 0; i < n; ++i) {
+    fwi_status s = check_call(b->plans[i], K[i]);
+    if (s != FWI_OK) return s;
+    key.insert(key.end(), {(uintptr_t)c[i], (uintptr_t)w[i], (uintptr_t)K[i], (uintptr_t)observed[i],
+                           (uintptr_t)observed_encoded[i], (uintptr_t)misfit[i], (uintptr_t)grad[i]});
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!b->exec || key != b->key) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    // capture on the batch's own stream: nothing runs during capture
+    cudaStream_t cs = b->origin;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    fwi_status s = FWI_OK;
+    if (cudaEventRecord(b->fork, cs) != cudaSuccess) s = FWI_ECUDA;
+    for (int i = 0; i < n && s == FWI_OK; ++i) {
+      if (cudaStreamWaitEvent(b->side[i], b->fork, 0) != cudaSuccess) { s = FWI_ECUDA; break; }
+      s = fwi_gradient(b->plans[i], c[i], w[i], K[i], observed[i], observed_encoded[i], misfit[i], grad[i],
+                       nullptr, b->side[i]);
+      if (s == FWI_OK && cudaEventRecord(b->join[i], b->side[i]) != cudaSuccess) s = FWI_ECUDA;
+      if (s == FWI_OK && cudaStreamWaitEvent(cs, b->join[i], 0) != cudaSuccess) s = FWI_ECUDA;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (s != FWI_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return s != FWI_OK ? s : FWI_ECUDA;
+    }
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    b->nodes = (int64_t)nn;
+    const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      b->exec = nullptr;
+      return FWI_ECUDA;
+    }
+    b->key = key;
+  }
+  for (int i = 0; i < n; ++i) {
+    b->plans[i]->last = st;
+    b->plans[i]->used = true;
+  }
+  CK(cudaGraphLaunch(b->exec, st));
+  return FWI_OK;
+}
+
+int64_t fwi_batch_nodes(const fwi_batch* b) { return b ? b->nodes : -1; }
+
+fwi_status fwi_batch_destroy(fwi_batch* b) {
+  if (!b) return FWI_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaStream_t s : b->side)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+  return FWI_OK;
+}
+
 fwi_status fwi_plan_destroy(fwi_plan* p) {
   if (p)
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);

@@ -30,7 +30,8 @@ PAIRING = {"literal": 0, "exact": 1}
 
 C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_gradient",
              "fwi_plan_status", "fwi_plan_voxel_steps", "fwi_plan_launches", "fwi_plan_profile",
-             "fwi_plan_profile_read", "fwi_adjoint_source_noalloc", "fwi_plan_destroy",
+             "fwi_plan_profile_read", "fwi_adjoint_source_noalloc", "fwi_batch_create",
+             "fwi_batch_gradient", "fwi_batch_nodes", "fwi_batch_destroy", "fwi_plan_destroy",
              "fwi_status_string")
 
 NOALLOC_MAX_PARTIALS = 8192
@@ -92,6 +93,16 @@ def lib():
         L.fwi_plan_profile_read.restype = ctypes.c_int
         L.fwi_adjoint_source_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp]
         L.fwi_adjoint_source_noalloc.restype = ctypes.c_int
+        L.fwi_batch_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.fwi_batch_create.restype = ctypes.c_int
+        L.fwi_batch_gradient.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32),
+                                         ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(vp),
+                                         ctypes.POINTER(vp), vp]
+        L.fwi_batch_gradient.restype = ctypes.c_int
+        L.fwi_batch_nodes.argtypes = [vp]
+        L.fwi_batch_nodes.restype = i64
+        L.fwi_batch_destroy.argtypes = [vp]
+        L.fwi_batch_destroy.restype = ctypes.c_int
         L.fwi_plan_destroy.argtypes = [vp]
         L.fwi_plan_destroy.restype = ctypes.c_int
         L.fwi_status_string.argtypes = [ctypes.c_int]
@@ -156,6 +167,28 @@ def fwi_adjoint_source_noalloc(traces_ptr, observed_ptr, K, nt, n_rec, qcum_ptr,
     cannot allocate device memory; see include/fwi.h for limits and sharing rules."""
     return lib().fwi_adjoint_source_noalloc(traces_ptr, observed_ptr, K, nt, n_rec, qcum_ptr,
                                             misfit_ptr, stream)
+
+
+def fwi_batch_create(plans):
+    arr = (ctypes.c_void_p * len(plans))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    out = ctypes.c_void_p(0)
+    st = lib().fwi_batch_create(len(plans), arr, ctypes.byref(out))
+    return st, out
+
+
+def fwi_batch_gradient(batch, c, w, K, observed, encoded, misfit, grad, stream) -> int:
+    n = len(c)
+    P = lambda xs: (ctypes.c_void_p * n)(*xs)
+    return lib().fwi_batch_gradient(batch, P(c), P(w), (ctypes.c_int32 * n)(*K), P(observed),
+                                    (ctypes.c_int32 * n)(*encoded), P(misfit), P(grad), stream)
+
+
+def fwi_batch_nodes(batch) -> int:
+    return lib().fwi_batch_nodes(batch)
+
+
+def fwi_batch_destroy(batch) -> int:
+    return lib().fwi_batch_destroy(batch)
 
 
 def fwi_plan_destroy(plan) -> int:
@@ -297,6 +330,48 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             fwi_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several plans (possibly of different grid sizes) run as one captured CUDA graph."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        st, self.handle = fwi_batch_create([p.handle for p in self.plans])
+        _check(st, "fwi_batch_create")
+
+    def gradient(self, cs, weights, observed, encoded=None, misfits=None, grads=None, stream=None):
+        n = len(self.plans)
+        encoded = encoded or [True] * n
+        if misfits is None:
+            misfits = [torch.empty(w.shape[0], dtype=torch.float64, device=c.device) for c, w in zip(cs, weights)]
+        if grads is None:
+            grads = [torch.empty(p.n_vox, dtype=torch.float64, device=c.device) for p, c in zip(self.plans, cs)]
+        st = fwi_batch_gradient(self.handle,
+                                [_dptr(c, torch.float32, "c").value for c in cs],
+                                [_dptr(w, torch.float32, "weights").value for w in weights],
+                                [w.shape[0] for w in weights],
+                                [_dptr(o, torch.float32, "observed").value for o in observed],
+                                [1 if e else 0 for e in encoded],
+                                [_dptr(m, torch.float64, "misfit").value for m in misfits],
+                                [_dptr(g, torch.float64, "grad").value for g in grads],
+                                _stream_handle(stream))
+        _check(st, "fwi_batch_gradient")
+        return misfits, grads
+
+    def nodes(self) -> int:
+        return fwi_batch_nodes(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fwi_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
