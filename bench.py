@@ -167,9 +167,15 @@ def run_batch(args):
         for wl in wls:
             wl.nt = args.nt
             wl.wavelet = wl.wavelet[:args.nt]
+    from paper_2102_00755_b300 import autotune
+    tuned = {}
+    for wl in wls:                      # one schedule per grid size, chosen by the autotuner
+        if (wl.nx, wl.ny, wl.nz) not in tuned:
+            tuned[(wl.nx, wl.ny, wl.nz)] = autotune.tune(wl, K=1, steps=24, reps=3, save=False)["schedule"]
     plans, plains, cs, ws, obs = [], [], [], [], []
     for wl in wls:
         plan = fwi.Plan.from_workload(wl, max_shots=1, device=dev)
+        autotune.set_schedule(plan, tuned[(wl.nx, wl.ny, wl.nz)])
         w = torch.tensor(wl.weights, dtype=torch.float32, device=dev)
         obs.append(plan.forward(torch.tensor(wl.c_true, dtype=torch.float32, device=dev).reshape(-1), w))
         plans.append(plan)
@@ -207,6 +213,8 @@ def run_batch(args):
     for p in plans:
         p.close()
     plains = [fwi.Plan.from_workload(wl, max_shots=1, sims_per_launch=1, device=dev) for wl in wls]
+    for p, wl in zip(plains, wls):
+        autotune.set_schedule(p, tuned[(wl.nx, wl.ny, wl.nz)])
 
     def plain():
         for p, c, w, o, D, g in zip(plains, cs, ws, obs, Ds, gs):
@@ -220,6 +228,7 @@ def run_batch(args):
            "config": {"workload": "batching: 16 encoded gradients of uneven grids (4 each of 64^3, "
                                   "96x96x48, 128x128x64, 160x160x80), 1200-2000 steps, one captured graph",
                       "voxel_steps_per_step": vsteps, "graph_nodes": batch.nodes(),
+                      "schedules": {"x".join(map(str, k)): v for k, v in tuned.items()},
                       "capture_and_first_run_s": capture_s},
            "gradients_per_h": 3600.0 * 16 / (ms_graph / 1e3),
            "sequential": {"value": G(ms_seq), "ms_per_step": ms_seq,
@@ -274,7 +283,10 @@ def main():
     if rank > 0:   # independent estimates per GPU (Sec. 4.5): other encoding weights
         rng = np.random.default_rng(1000 + rank)
         wl.weights = np.stack([synth.rademacher(len(wl.src_idx), rng) for _ in range(K)])
+    from paper_2102_00755_b300 import autotune
+    schedule = autotune.tune(wl, K=K, steps=24, reps=3, device=dev, save=False)["schedule"]
     plan = fwi.Plan.from_workload(wl, pairing="literal", max_shots=K, device=dev)
+    autotune.set_schedule(plan, schedule)
     c_true = torch.tensor(wl.c_true, dtype=torch.float32, device=dev).reshape(-1)
     c_model = torch.tensor(wl.c_model, dtype=torch.float32, device=dev).reshape(-1)
     w = torch.tensor(wl.weights, dtype=torch.float32, device=dev)
@@ -348,6 +360,7 @@ def main():
     plain = None
     if args.plain_steps > 0:
         pplan = fwi.Plan.from_workload(wl, pairing="literal", max_shots=K, sims_per_launch=1, device=dev)
+        autotune.set_schedule(pplan, schedule)
         pplan.gradient(c_model, w, observed, misfit=misfit, grad=grad)
         torch.cuda.synchronize(dev)
         pt = []
@@ -412,7 +425,7 @@ def main():
         "config": {"workload": WORKLOAD, "grid": [wl.nx, wl.ny, wl.nz], "nt": wl.nt,
                    "super_shots": K, "n_src": int(len(wl.src_idx)), "n_rec": int(len(wl.rec_idx)),
                    "n_gamma": int(len(wl.gamma_idx)), "n_layer": int(len(wl.layer_idx)),
-                   "pairing": "literal", "voxel_steps_per_step": vsteps,
+                   "pairing": "literal", "voxel_steps_per_step": vsteps, "fft_schedule": schedule,
                    "l2": "256 MB buffer written between timed steps; working set > 126 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gradients_per_h": grads_per_h,

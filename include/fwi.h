@@ -149,6 +149,27 @@ int64_t fwi_plan_voxel_steps(const fwi_plan *plan, int32_t K, int32_t gradient);
 /* Number of kernel launches one call issues (for launch accounting). */
 int64_t fwi_plan_launches(const fwi_plan *plan, int32_t K, int32_t gradient);
 
+/*
+ * FFT schedule of a plan (what the autotuner searches).
+ *   specialized: 1 = compile-time transforms where this build has them (square planes
+ *                of 32, 64, 96, 128, 160; z lengths 32..128), 0 = runtime schedules
+ *   radix_order: runtime radix schedule: 0 = radix 8, 4, 2 then 3, 5; 1 = radix 4, 2
+ *                then 3, 5 (no radix 8); 2 = small radices first (2, 3, 4, 5, 8 order
+ *                reversed: the largest pass last)
+ *   z_tile:      spectrum columns per z-pass CTA, 16 or 32
+ * fwi_plan_create picks {1, 0, 32}.  Setting a schedule keeps the workspace size;
+ * it may be changed after binding (between calls).  Results differ only by FP32
+ * rounding order.  Errors: FWI_EINVAL (bad values), FWI_ENOTSUP (the shared memory
+ * the schedule needs exceeds the device limit).
+ */
+typedef struct fwi_schedule {
+  int32_t specialized;
+  int32_t radix_order;
+  int32_t z_tile;
+} fwi_schedule;
+fwi_status fwi_plan_set_schedule(fwi_plan *plan, const fwi_schedule *schedule);
+fwi_status fwi_plan_get_schedule(const fwi_plan *plan, fwi_schedule *schedule);
+
 /* Kernels that can be timed by the profiling hook. */
 typedef enum fwi_kernel {
   FWI_K_ZPASS_MOMENTUM = 0, FWI_K_PLANE_MOMENTUM = 1, FWI_K_ZPASS_MASS = 2, FWI_K_PLANE_MASS = 3

@@ -149,14 +149,19 @@ __global__ void k_grad_final(const double* __restrict__ acc, const int* __restri
 }
 
 // ------------------------------------------------------------ host helpers
-bool factor235(int n, AxisPlan* A) {
+// Radix schedule of one axis: order 0 = 8, 4, 2, 3, 5; 1 = 4, 2, 3, 5 (no 8);
+// 2 = the order-0 passes reversed (largest radix last).
+bool factor235(int n, AxisPlan* A, int order = 0) {
   int m = n, ns = 0;
-  while (m % 8 == 0) { A->radix[ns++] = 8; m /= 8; }
-  while (m % 4 == 0) { A->radix[ns++] = 4; m /= 4; }
-  while (m % 2 == 0) { A->radix[ns++] = 2; m /= 2; }
-  while (m % 3 == 0) { A->radix[ns++] = 3; m /= 3; }
-  while (m % 5 == 0) { A->radix[ns++] = 5; m /= 5; }
+  int r[kMaxStages + 8];
+  if (order != 1)
+    while (m % 8 == 0) { r[ns++] = 8; m /= 8; }
+  while (m % 4 == 0) { r[ns++] = 4; m /= 4; }
+  while (m % 2 == 0) { r[ns++] = 2; m /= 2; }
+  while (m % 3 == 0) { r[ns++] = 3; m /= 3; }
+  while (m % 5 == 0) { r[ns++] = 5; m /= 5; }
   if (m != 1 || ns > kMaxStages) return false;
+  for (int s = 0; s < ns; ++s) A->radix[s] = order == 2 ? r[ns - 1 - s] : r[s];
   A->n = n;
   A->nstages = ns;
   return true;
@@ -261,6 +266,7 @@ struct fwi_plan {
   int fxy;   // specialised plane side (0: runtime schedules)
   int fz;    // specialised z length (0: runtime schedules)
   int tz;    // z-pass tile width (columns)
+  fwi_schedule sched;
   // host tables
   std::vector<float2> tw, ap[3], am[3];
   std::vector<float> kx2, ky2, kz2, lam[3], lams[3], wavelet;
@@ -370,7 +376,7 @@ void base_params(fwi_plan* p, StepParams* P) {
       if ((p)->epl == 8) { constexpr int E = 8, F = 0; CALL; }          \
       else { constexpr int E = 16, F = 0; CALL; }                       \
   }
-#define Z_DISPATCH(p, CALL)                                             \
+#define Z_DISPATCH_T(p, TZ, CALL)                                       \
   switch ((p)->fz) {                                                    \
     case 32: { constexpr int E = 8, FZ = 32; CALL; } break;             \
     case 48: { constexpr int E = 8, FZ = 48; CALL; } break;             \
@@ -382,6 +388,9 @@ void base_params(fwi_plan* p, StepParams* P) {
       if ((p)->epl == 8) { constexpr int E = 8, FZ = 0; CALL; }         \
       else { constexpr int E = 16, FZ = 0; CALL; }                      \
   }
+#define Z_DISPATCH(p, CALL)                                             \
+  if ((p)->tz == 32) { constexpr int TZ = 32; Z_DISPATCH_T(p, TZ, CALL) } \
+  else { constexpr int TZ = 16; Z_DISPATCH_T(p, TZ, CALL) }
 
 template <int E, int F>
 void set_attrs_plane(fwi_plan* p) {
@@ -389,14 +398,14 @@ void set_attrs_plane(fwi_plan* p) {
   cudaFuncSetAttribute(k_plane_mass<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_mass);
   cudaFuncSetAttribute(k_tr_init<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_plane);
 }
-template <int E, int FZ>
+template <int E, int FZ, int TZ>
 void set_attrs_z(fwi_plan* p) {
-  cudaFuncSetAttribute(k_zpass<0, E, FZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmom);
-  cudaFuncSetAttribute(k_zpass<1, E, FZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmass);
+  cudaFuncSetAttribute(k_zpass<0, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmom);
+  cudaFuncSetAttribute(k_zpass<1, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmass);
 }
 void set_attrs(fwi_plan* p) {
   PLANE_DISPATCH(p, (set_attrs_plane<E, F>(p)));
-  Z_DISPATCH(p, (set_attrs_z<E, FZ>(p)));
+  Z_DISPATCH(p, (set_attrs_z<E, FZ, TZ>(p)));
 }
 
 void prof_begin(fwi_plan* p, int kernel, cudaStream_t st, int nsims, int* slot) {
@@ -418,13 +427,13 @@ void launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) {
   const dim3 gp(p->prob.nz, P.nsims);
   int slot;
   prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
-  Z_DISPATCH(p, (k_zpass<0, E, FZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+  Z_DISPATCH(p, (k_zpass<0, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
   PLANE_DISPATCH(p, (k_plane_mom<E, F, F><<<gp, kTpbPlane, p->smem_plane, st>>>(P)));
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
-  Z_DISPATCH(p, (k_zpass<1, E, FZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+  Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
   PLANE_DISPATCH(p, (k_plane_mass<E, F, F><<<gp, kTpbPlane, p->smem_mass, st>>>(P)));
@@ -449,6 +458,50 @@ void launch_step(fwi_plan* p, const StepParams& P, cudaStream_t st) {
     }
     launch_step_batch(p, Q, st);
   }
+}
+
+// Launch shapes and shared-memory sizes of the plan's current schedule.
+fwi_status apply_schedule(fwi_plan* p) {
+  const fwi_problem& q = p->prob;
+  const fwi_schedule& sc = p->sched;
+  p->epl = std::max(q.nx, std::max(q.ny, q.nz)) <= 256 ? 8 : 16;
+  auto in = [](int v, std::initializer_list<int> l) {
+    for (int x : l)
+      if (x == v) return true;
+    return false;
+  };
+  p->fxy = (sc.specialized && q.nx == q.ny && in(q.nx, {32, 64, 96, 128, 160})) ? q.nx : 0;
+  p->fz = (sc.specialized && in(q.nz, {32, 48, 64, 80, 96, 128})) ? q.nz : 0;
+  p->tz = sc.z_tile;
+  const int tw_x = p->ax.tw_off, tw_y = p->ay.tw_off, tw_z = p->az.tw_off;
+  if (!factor235(q.nx, &p->ax, sc.radix_order) || !factor235(q.ny, &p->ay, sc.radix_order) ||
+      !factor235(q.nz, &p->az, sc.radix_order))
+    return FWI_ENOTSUP;
+  p->ax.tw_off = tw_x;
+  p->ay.tw_off = tw_y;
+  p->az.tw_off = tw_z;
+  const int ntw = ((q.nx + q.ny + 31) & ~31);
+  // pair lines per warp group: momentum (x work budget 256) and mass (128)
+  auto group = [&](int budget) {
+    int g = 1;
+    if (p->fxy > 0) {
+      while (2 * g <= budget / p->fxy) g *= 2;
+    } else {
+      g = std::max(1, (budget / 256) * 16 * p->epl / p->hx);
+    }
+    return g;
+  };
+  const size_t base = ((size_t)ntw + (size_t)p->npair * 2 * p->hx) * sizeof(float2);
+  const size_t warps = kTpbPlane / 32;
+  p->smem_plane = base + warps * 1 * 2 * group(256) * q.nx * 4;   // one staged array
+  p->smem_mass = base + warps * 4 * 2 * group(128) * q.nx * 4;    // four staged arrays
+  const size_t ztw = (size_t)((q.nz + 31) & ~31);
+  p->smem_zmom = (ztw + (size_t)(2 * p->tz + 4) * q.nz) * sizeof(float2);
+  p->smem_zmass = (ztw + (size_t)(3 * p->tz + 4) * q.nz) * sizeof(float2);
+  if (std::max(q.nx, std::max(q.ny, q.nz)) > 512 || p->smem_mass > 227 * 1024 ||
+      p->smem_zmass > 227 * 1024)
+    return FWI_ENOTSUP;
+  return FWI_OK;
 }
 
 fwi_status zero_sim(fwi_plan* p, int s, cudaStream_t st) {
@@ -614,37 +667,11 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   }
 
   // launch shapes: every axis must fit one warp group (n <= 512)
-  p->epl = std::max(q.nx, std::max(q.ny, q.nz)) <= 256 ? 8 : 16;
-  auto in = [](int v, std::initializer_list<int> l) { for (int x : l) if (x == v) return true; return false; };
-  p->fxy = (q.nx == q.ny && in(q.nx, {32, 64, 96, 128, 160})) ? q.nx : 0;
-  p->fz = in(q.nz, {32, 48, 64, 80, 96, 128}) ? q.nz : 0;
-  p->tz = p->fz > 0 ? 32 : 16;
-  const int ntw = ((q.nx + q.ny + 31) & ~31);
-  {
-    // pair lines per warp group: momentum (x work budget 256) and mass (128)
-    auto group = [&](int budget) {
-      int g = 1;
-      if (p->fxy > 0) {
-        while (2 * g <= budget / p->fxy) g *= 2;
-      } else {
-        g = std::max(1, (budget / 256) * 16 * p->epl / p->hx);
-      }
-      return g;
-    };
-    const size_t base = ((size_t)ntw + (size_t)p->npair * 2 * p->hx) * sizeof(float2);
-    const size_t warps = kTpbPlane / 32;
-    p->smem_plane = base + warps * 1 * 2 * group(256) * q.nx * 4;   // one staged array
-    p->smem_mass = base + warps * 4 * 2 * group(128) * q.nx * 4;    // four staged arrays
-  }
-  const size_t ztw = (size_t)((q.nz + 31) & ~31);
-  p->smem_zmom = (ztw + (size_t)(2 * p->tz + 4) * q.nz) * sizeof(float2);
-  p->smem_zmass = (ztw + (size_t)(3 * p->tz + 4) * q.nz) * sizeof(float2);
-  if (std::max(q.nx, std::max(q.ny, q.nz)) > 512 || p->smem_mass > 227 * 1024 ||
-      p->smem_zmass > 227 * 1024) {
+  p->sched = fwi_schedule{1, 0, 32};
+  if (apply_schedule(p) != FWI_OK) {
     delete p;
     return FWI_ENOTSUP;
   }
-
   // workspace layout
   Layout& L = p->L;
   const int K = p->K, nt = q.nt;
@@ -1044,6 +1071,28 @@ fwi_status fwi_batch_destroy(fwi_batch* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->origin) cudaStreamDestroy(b->origin);
   delete b;
+  return FWI_OK;
+}
+
+fwi_status fwi_plan_set_schedule(fwi_plan* p, const fwi_schedule* sc) {
+  if (!p || !sc) return FWI_EINVAL;
+  if ((sc->specialized != 0 && sc->specialized != 1) || sc->radix_order < 0 || sc->radix_order > 2 ||
+      (sc->z_tile != 16 && sc->z_tile != 32))
+    return FWI_EINVAL;
+  const fwi_schedule old = p->sched;
+  p->sched = *sc;
+  if (apply_schedule(p) != FWI_OK) {
+    p->sched = old;
+    apply_schedule(p);
+    return FWI_ENOTSUP;
+  }
+  if (p->ws) set_attrs(p);
+  return FWI_OK;
+}
+
+fwi_status fwi_plan_get_schedule(const fwi_plan* p, fwi_schedule* sc) {
+  if (!p || !sc) return FWI_EINVAL;
+  *sc = p->sched;
   return FWI_OK;
 }
 

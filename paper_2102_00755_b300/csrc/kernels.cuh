@@ -284,9 +284,9 @@ __device__ __forceinline__ void forward_y_and_store(float2* sm, const float2* tw
 // A CTA holds TZ adjacent (ky, kx) columns of every slot for all z; the row
 // stride RS = slots * TZ + 4 keeps the lanes of a warp (adjacent columns, then
 // z) on distinct banks.  FZ > 0: specialised z transforms (nz = FZ).
-template <int EPL, int FZ>
+template <int EPL, int FZ, int TZc>
 struct ZCfg {
-  static constexpr int TZ = FZ > 0 ? 32 : 16;
+  static constexpr int TZ = TZc;
   static constexpr int GZc = FZ > 0 ? pow2_floor(256 / FZ < 32 ? 256 / FZ : 32) : 0;
   __device__ static int gz(int nz) { return FZ > 0 ? GZc : min(lines_per_group<EPL>(nz), TZ); }
   template <bool INV>
@@ -297,10 +297,10 @@ struct ZCfg {
   }
 };
 
-template <int MODE, int EPL, int FZ>
+template <int MODE, int EPL, int FZ, int TZc>
 __global__ void __launch_bounds__(kTpbZ, 2) k_zpass(const __grid_constant__ StepParams P) {
   if (*P.bad) return;
-  using C = ZCfg<EPL, FZ>;
+  using C = ZCfg<EPL, FZ, TZc>;
   constexpr int TZ = C::TZ;
   extern __shared__ float2 zsm_raw[];
   const SimPtrs& S = P.sims[blockIdx.y];

@@ -30,7 +30,8 @@ PAIRING = {"literal": 0, "exact": 1}
 
 C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_gradient",
              "fwi_plan_status", "fwi_plan_voxel_steps", "fwi_plan_launches", "fwi_plan_profile",
-             "fwi_plan_profile_read", "fwi_adjoint_source_noalloc", "fwi_batch_create",
+             "fwi_plan_profile_read", "fwi_plan_set_schedule", "fwi_plan_get_schedule",
+             "fwi_adjoint_source_noalloc", "fwi_batch_create",
              "fwi_batch_gradient", "fwi_batch_nodes", "fwi_batch_destroy", "fwi_plan_destroy",
              "fwi_status_string")
 
@@ -43,6 +44,10 @@ class FwiError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
         super().__init__(f"{where}: {fwi_status_string(status)} (status {status})")
+
+
+class fwi_schedule(ctypes.Structure):
+    _fields_ = [("specialized", ctypes.c_int32), ("radix_order", ctypes.c_int32), ("z_tile", ctypes.c_int32)]
 
 
 class fwi_problem(ctypes.Structure):
@@ -93,6 +98,10 @@ def lib():
         L.fwi_plan_profile_read.restype = ctypes.c_int
         L.fwi_adjoint_source_noalloc.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp]
         L.fwi_adjoint_source_noalloc.restype = ctypes.c_int
+        L.fwi_plan_set_schedule.argtypes = [vp, ctypes.POINTER(fwi_schedule)]
+        L.fwi_plan_set_schedule.restype = ctypes.c_int
+        L.fwi_plan_get_schedule.argtypes = [vp, ctypes.POINTER(fwi_schedule)]
+        L.fwi_plan_get_schedule.restype = ctypes.c_int
         L.fwi_batch_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
         L.fwi_batch_create.restype = ctypes.c_int
         L.fwi_batch_gradient.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32),
@@ -167,6 +176,14 @@ def fwi_adjoint_source_noalloc(traces_ptr, observed_ptr, K, nt, n_rec, qcum_ptr,
     cannot allocate device memory; see include/fwi.h for limits and sharing rules."""
     return lib().fwi_adjoint_source_noalloc(traces_ptr, observed_ptr, K, nt, n_rec, qcum_ptr,
                                             misfit_ptr, stream)
+
+
+def fwi_plan_set_schedule(plan, schedule: fwi_schedule) -> int:
+    return lib().fwi_plan_set_schedule(plan, ctypes.byref(schedule))
+
+
+def fwi_plan_get_schedule(plan, schedule: fwi_schedule) -> int:
+    return lib().fwi_plan_get_schedule(plan, ctypes.byref(schedule))
 
 
 def fwi_batch_create(plans):

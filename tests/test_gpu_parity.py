@@ -135,3 +135,34 @@ def test_call_argument_errors():
     with pytest.raises(fwi.FwiError) as e:
         plan.forward(dev(wl.c_model), dev(wl.weights))     # K = 2 > max_shots
     assert e.value.status == fwi.FWI_EINVAL
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 18), (32, 32, 32)])
+def test_every_fft_schedule_meets_parity(shape):
+    """Every schedule the autotuner may pick (specialised or runtime radix schedules in
+    each order, both z tiles) gives oracle-parity traces."""
+    from paper_2102_00755_b300 import autotune
+    wl = synth.small_workload(*shape, 40, pml=4, n_src=2, n_rec=16, K=1, seed=4)
+    ref = oc.forward(wl, wl.c_model, wl.weights)
+    plan = fwi.Plan.from_workload(wl, max_shots=1)
+    seen = 0
+    for cand in autotune.CANDIDATES:
+        if autotune.set_schedule(plan, cand) != fwi.FWI_OK:
+            continue
+        assert autotune.get_schedule(plan) == cand
+        tr = plan.forward(dev(wl.c_model), dev(wl.weights)).cpu().numpy()
+        assert oc.rel(tr[0], ref[0]) < TOL_TRACES, cand
+        seen += 1
+    assert seen >= 6
+
+
+def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
+    from paper_2102_00755_b300 import autotune
+    monkeypatch.setenv("FWI_SCHEDULE_CACHE", str(tmp_path / "s.json"))
+    wl = synth.small_workload(32, 32, 32, 40, pml=4, n_src=2, n_rec=16, K=1, seed=4)
+    res = autotune.tune(wl, K=1, steps=8, reps=1)
+    assert res["schedule"] in [{k: c[k] for k in ("specialized", "radix_order", "z_tile")}
+                               for c in autotune.CANDIDATES]
+    plan = fwi.Plan.from_workload(wl, max_shots=1)
+    assert autotune.apply_cached(plan, 32, 32, 32, 1)
+    assert autotune.get_schedule(plan) == res["schedule"]
