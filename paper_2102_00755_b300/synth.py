@@ -275,6 +275,23 @@ def config4() -> Workload:
     return phantom_workload("diff-96x96x48", 96, 96, 48, 1000, 32, 128, 1, 100, (101,))
 
 
+def smooth_direction(wl: Workload, seed: int, n_terms: int = 4) -> np.ndarray:
+    """Seeded smooth perturbation direction supported in Gamma: a sum of n_terms
+    low-order 3D cosines (wavenumbers 0..3 per axis, random phases) restricted to
+    Gamma and scaled to max |.| = 1.  Shape (nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    X, Y, Z = coords((wl.nx, wl.ny, wl.nz))
+    d = np.zeros(wl.shape)
+    for _ in range(n_terms):
+        k = rng.integers(0, 4, size=3)
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        d += np.cos(2.0 * math.pi * (k[0] * X / wl.nx + k[1] * Y / wl.ny + k[2] * Z / wl.nz) + ph)
+    m = np.zeros(wl.n_vox)
+    m[wl.gamma_idx] = 1.0
+    d *= m.reshape(wl.shape)
+    return d / np.abs(d).max()
+
+
 SERVING_LEVELS = {
     # physical voxels, dx, steps; the PML is added outside by the App. B size rule
     0: ((111, 111, 56), 2.0e-3, 1000),
