@@ -247,6 +247,10 @@ fwi_status fwi_plan_destroy(fwi_plan *plan);
 /* Static description of a status code. */
 const char *fwi_status_string(fwi_status status);
 
+/* Name and description of the last CUDA runtime error that made a call of this
+ * thread return FWI_ECUDA ("" if none).  Valid until the thread's next call. */
+const char *fwi_last_cuda_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -355,10 +355,25 @@ void base_params(fwi_plan* p, StepParams* P) {
   P->ring = at<float>(p, p->o_ring);
 }
 
-#define CK(x)                                   \
-  do {                                          \
-    cudaError_t e_ = (x);                       \
-    if (e_ != cudaSuccess) return FWI_ECUDA;    \
+thread_local char g_last_cuda_error[256] = "";
+
+fwi_status cuda_fail(cudaError_t e, const char* what) {
+  std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s (%s)", what, cudaGetErrorName(e),
+                cudaGetErrorString(e));
+  return FWI_ECUDA;
+}
+
+#define CK(x)                                       \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
+  } while (0)
+
+// after a kernel launch: report a launch failure with the launch site's name
+#define LAUNCHED(label)                                        \
+  do {                                                         \
+    cudaError_t e_ = cudaGetLastError();                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, "launch " label); \
   } while (0)
 
 // Kernel instantiations: specialised transforms for square planes of side FXY in
@@ -392,20 +407,43 @@ void base_params(fwi_plan* p, StepParams* P) {
   if ((p)->tz == 32) { constexpr int TZ = 32; Z_DISPATCH_T(p, TZ, CALL) } \
   else { constexpr int TZ = 16; Z_DISPATCH_T(p, TZ, CALL) }
 
+// The dynamic shared-memory cap is a per-kernel (not per-plan) attribute shared by
+// every plan that launches the same instantiation, so it is set to the device's
+// opt-in maximum, never to one plan's size; each launch still requests only what
+// its plan needs, which is what sets occupancy.
+int smem_optin_max() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v > 0 ? v : 48 * 1024;
+}
+
 template <int E, int F>
-void set_attrs_plane(fwi_plan* p) {
-  cudaFuncSetAttribute(k_plane_mom<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_plane);
-  cudaFuncSetAttribute(k_plane_mass<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_mass);
-  cudaFuncSetAttribute(k_tr_init<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_plane);
+void set_attrs_plane(int cap) {
+  cudaFuncSetAttribute(k_plane_mom<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_plane_mass<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_tr_init<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 template <int E, int FZ, int TZ>
-void set_attrs_z(fwi_plan* p) {
-  cudaFuncSetAttribute(k_zpass<0, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmom);
-  cudaFuncSetAttribute(k_zpass<1, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_zmass);
+void set_attrs_z(int cap) {
+  cudaFuncSetAttribute(k_zpass<0, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_zpass<1, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 void set_attrs(fwi_plan* p) {
-  PLANE_DISPATCH(p, (set_attrs_plane<E, F>(p)));
-  Z_DISPATCH(p, (set_attrs_z<E, FZ, TZ>(p)));
+  const int cap = smem_optin_max();
+  PLANE_DISPATCH(p, (set_attrs_plane<E, F>(cap)));
+  Z_DISPATCH(p, (set_attrs_z<E, FZ, TZ>(cap)));
+  // Touch every small kernel too, so that modules are loaded before any stream
+  // capture of a call (a first launch inside a capture may not load them).
+  cudaFuncAttributes a;
+  cudaFuncGetAttributes(&a, k_prepare_c);
+  cudaFuncGetAttributes(&a, k_prepare_coefs);
+  cudaFuncGetAttributes(&a, k_source_amp);
+  cudaFuncGetAttributes(&a, k_encode);
+  cudaFuncGetAttributes(&a, k_misfit);
+  cudaFuncGetAttributes(&a, k_misfit_final);
+  cudaFuncGetAttributes(&a, k_accumulate);
+  cudaFuncGetAttributes(&a, k_grad_final);
 }
 
 void prof_begin(fwi_plan* p, int kernel, cudaStream_t st, int nsims, int* slot) {
@@ -422,32 +460,34 @@ void prof_end(fwi_plan* p, cudaStream_t st, int slot) {
 }
 
 // One time step for a batch of simulations (four launches).
-void launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) {
+fwi_status launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) {
   const dim3 gz((p->mspec + p->tz - 1) / p->tz, P.nsims);
   const dim3 gp(p->prob.nz, P.nsims);
   int slot;
   prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
   Z_DISPATCH(p, (k_zpass<0, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+  LAUNCHED("k_zpass<momentum>");
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
   PLANE_DISPATCH(p, (k_plane_mom<E, F, F><<<gp, kTpbPlane, p->smem_plane, st>>>(P)));
+  LAUNCHED("k_plane_mom");
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
   Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+  LAUNCHED("k_zpass<mass>");
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
   PLANE_DISPATCH(p, (k_plane_mass<E, F, F><<<gp, kTpbPlane, p->smem_mass, st>>>(P)));
+  LAUNCHED("k_plane_mass");
   prof_end(p, st, slot);
+  return FWI_OK;
 }
 
 // One time step: all simulations in one launch sequence, or (plain form) one
 // launch sequence per simulation.
-void launch_step(fwi_plan* p, const StepParams& P, cudaStream_t st) {
+fwi_status launch_step(fwi_plan* p, const StepParams& P, cudaStream_t st) {
   const int spl = p->prob.sims_per_launch;
-  if (spl <= 0 || spl >= P.nsims) {
-    launch_step_batch(p, P, st);
-    return;
-  }
+  if (spl <= 0 || spl >= P.nsims) return launch_step_batch(p, P, st);
   for (int s0 = 0; s0 < P.nsims; s0 += spl) {
     StepParams Q = P;
     Q.nsims = std::min(spl, P.nsims - s0);
@@ -456,8 +496,10 @@ void launch_step(fwi_plan* p, const StepParams& P, cudaStream_t st) {
       Q.tidx[i] = P.tidx[s0 + i];
       Q.slot[i] = P.slot[s0 + i];
     }
-    launch_step_batch(p, Q, st);
+    const fwi_status s = launch_step_batch(p, Q, st);
+    if (s != FWI_OK) return s;
   }
+  return FWI_OK;
 }
 
 // Launch shapes and shared-memory sizes of the plan's current schedule.
@@ -514,12 +556,13 @@ fwi_status prepare(fwi_plan* p, const float* c, cudaStream_t st) {
   const fwi_problem& q = p->prob;
   CK(cudaMemsetAsync(p->ws + p->o_bad, 0, sizeof(int), st));
   k_prepare_c<<<592, 256, 0, st>>>(c, at<float>(p, p->o_c2), p->nvox, (float)q.c_ref, at<int>(p, p->o_bad));
+  LAUNCHED("k_prepare_c");
   k_prepare_coefs<<<148, 256, 0, st>>>(c, q.dt, q.dx, at<int>(p, p->o_us_vox), p->n_us,
                                        at<float>(p, p->o_us_coef), at<int>(p, p->o_ur_vox), p->n_ur,
                                        at<float>(p, p->o_ur_coef), at<int>(p, p->o_gam_vox), q.n_gamma,
                                        at<float>(p, p->o_coefG), at<int>(p, p->o_lay_vox), q.n_layer,
                                        at<float>(p, p->o_inv3c2));
-  CK(cudaGetLastError());
+  LAUNCHED("k_prepare_coefs");
   return FWI_OK;
 }
 
@@ -529,6 +572,7 @@ fwi_status run_forward(fwi_plan* p, const float* w, int K, bool record_layer, fl
   k_source_amp<<<dim3(q.nt, K), 128, 0, st>>>(w, q.n_src, at<float>(p, p->o_us_coef),
                                               at<int>(p, p->o_us_mptr), at<int>(p, p->o_us_mem), p->n_us,
                                               at<float>(p, p->o_wav), q.nt, at<float>(p, p->o_amp));
+  LAUNCHED("k_source_amp");
   StepParams P;
   base_params(p, &P);
   P.record_layer = record_layer ? 1 : 0;
@@ -541,13 +585,16 @@ fwi_status run_forward(fwi_plan* p, const float* w, int K, bool record_layer, fl
   }
   for (int n = 0; n < q.nt; ++n) {
     for (int k = 0; k < K; ++k) P.tidx[k] = n;
-    launch_step(p, P, st);
+    const fwi_status s = launch_step(p, P, st);
+    if (s != FWI_OK) return s;
   }
-  CK(cudaGetLastError());
   return FWI_OK;
 }
 
 fwi_status check_call(fwi_plan* p, int K) {
+  // A non-sticky error left by another library would otherwise be reported as
+  // ours by the launch checks below; faults that poison the context persist.
+  (void)cudaGetLastError();
   if (!p || !p->ws) return FWI_EINVAL;
   if (K < 1 || K > p->K) return FWI_EINVAL;
   return FWI_OK;
@@ -556,6 +603,8 @@ fwi_status check_call(fwi_plan* p, int K) {
 }  // namespace
 
 extern "C" {
+
+const char* fwi_last_cuda_error(void) { return g_last_cuda_error; }
 
 const char* fwi_status_string(fwi_status s) {
   switch (s) {
@@ -788,6 +837,7 @@ fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32
   if (!observed_encoded) {
     const int64_t per = (int64_t)nt * q.n_rec;
     k_encode<<<592, 256, 0, st>>>(observed, weights, q.n_src, K, per, at<float>(p, p->o_obs));
+    LAUNCHED("k_encode");
     obs = at<float>(p, p->o_obs);
   }
   // forward, recording traces and the boundary-layer history
@@ -795,7 +845,9 @@ fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32
   // residual, misfit, cumulative sum
   k_misfit<<<dim3(p->nblk_misfit, K), 256, 0, st>>>(at<float>(p, p->o_traces), obs, nt, q.n_rec,
                                                     at<float>(p, p->o_qf), at<double>(p, p->o_dpart));
+  LAUNCHED("k_misfit");
   k_misfit_final<<<1, 32, 0, st>>>(at<double>(p, p->o_dpart), p->nblk_misfit, K, misfit);
+  LAUNCHED("k_misfit_final");
   CK(cudaMemsetAsync(p->ws + p->o_acc, 0, (size_t)K * q.n_gamma * 8, st));
   // adjoint sims 0..K-1 and TR sims K..2K-1
   StepParams P;
@@ -815,7 +867,8 @@ fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32
     T.slot[k] = 1;
   }
   PLANE_DISPATCH(p, (k_tr_init<E, F, F><<<dim3(q.nz, K), kTpbPlane, p->smem_plane, st>>>(T)));
-  launch_step(p, T, st);
+  LAUNCHED("k_tr_init");
+  if ((s = launch_step(p, T, st)) != FWI_OK) return s;
   // interleaved adjoint and TR iterations
   const bool exact = q.pairing == FWI_PAIRING_EXACT;
   const int nit = exact ? Nt + 1 : Nt - 1;
@@ -838,16 +891,18 @@ fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32
         CK(cudaMemsetAsync(at<float>(p, p->o_ring) + ((size_t)k * 3 + slot) * q.n_gamma, 0,
                            (size_t)q.n_gamma * 4, st));
     }
-    launch_step(p, S, st);
+    if ((s = launch_step(p, S, st)) != FWI_OK) return s;
     k_accumulate<<<dim3(nblk, K), 256, 0, st>>>(at<float>(p, p->o_ring), at<float>(p, p->o_pa),
                                                 at<float>(p, p->o_coefG), q.n_gamma, it % 3, (it + 1) % 3,
                                                 (it + 2) % 3, at<double>(p, p->o_acc), at<int>(p, p->o_bad));
+    LAUNCHED("k_accumulate");
   }
   // mean over shots, scaled to dD/dc if requested
   const double scale = q.c_rec > 0 ? q.dx * q.c_rec / 2.0 : 1.0;
   CK(cudaMemsetAsync(grad, 0, (size_t)p->nvox * 8, st));
   k_grad_final<<<(q.n_gamma + 255) / 256, 256, 0, st>>>(at<double>(p, p->o_acc), at<int>(p, p->o_gam_vox),
                                                         q.n_gamma, K, scale, grad);
+  LAUNCHED("k_grad_final");
   if (traces)
     CK(cudaMemcpyAsync(traces, p->ws + p->o_traces, (size_t)K * nt * q.n_rec * 4,
                        cudaMemcpyDeviceToDevice, st));

@@ -33,7 +33,7 @@ C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_g
              "fwi_plan_profile_read", "fwi_plan_set_schedule", "fwi_plan_get_schedule",
              "fwi_adjoint_source_noalloc", "fwi_batch_create",
              "fwi_batch_gradient", "fwi_batch_nodes", "fwi_batch_destroy", "fwi_plan_destroy",
-             "fwi_status_string")
+             "fwi_status_string", "fwi_last_cuda_error")
 
 NOALLOC_MAX_PARTIALS = 8192
 
@@ -43,7 +43,10 @@ KERNELS = {"zpass_momentum": 0, "plane_momentum": 1, "zpass_mass": 2, "plane_mas
 class FwiError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__(f"{where}: {fwi_status_string(status)} (status {status})")
+        extra = ""
+        if status == FWI_ECUDA:
+            extra = " [" + lib().fwi_last_cuda_error().decode() + "]"
+        super().__init__(f"{where}: {fwi_status_string(status)} (status {status}){extra}")
 
 
 class fwi_schedule(ctypes.Structure):
@@ -114,6 +117,8 @@ def lib():
         L.fwi_batch_destroy.restype = ctypes.c_int
         L.fwi_plan_destroy.argtypes = [vp]
         L.fwi_plan_destroy.restype = ctypes.c_int
+        L.fwi_last_cuda_error.argtypes = []
+        L.fwi_last_cuda_error.restype = ctypes.c_char_p
         L.fwi_status_string.argtypes = [ctypes.c_int]
         L.fwi_status_string.restype = ctypes.c_char_p
         _lib = L

@@ -166,3 +166,16 @@ def test_autotuner_picks_and_caches(tmp_path, monkeypatch):
     plan = fwi.Plan.from_workload(wl, max_shots=1)
     assert autotune.apply_cached(plan, 32, 32, 32, 1)
     assert autotune.get_schedule(plan) == res["schedule"]
+
+
+def test_plans_of_different_sizes_coexist():
+    """A plan bound after a larger one must not restrict the larger plan's launches
+    (kernel attributes are shared by every plan using the same kernel)."""
+    big = synth.small_workload(48, 40, 30, 30, pml=5, n_src=2, n_rec=12, K=1, seed=22)
+    small = synth.small_workload(32, 32, 24, 30, pml=4, n_src=2, n_rec=12, K=1, seed=21)
+    p_big = fwi.Plan.from_workload(big, max_shots=1)
+    ref = p_big.forward(dev(big.c_model), dev(big.weights)).clone()
+    p_small = fwi.Plan.from_workload(small, max_shots=1)
+    p_small.forward(dev(small.c_model), dev(small.weights))
+    again = p_big.forward(dev(big.c_model), dev(big.weights))
+    assert torch.equal(ref, again)
