@@ -157,7 +157,10 @@ int64_t fwi_plan_launches(const fwi_plan *plan, int32_t K, int32_t gradient);
  *                then 3, 5 (no radix 8); 2 = small radices first (2, 3, 4, 5, 8 order
  *                reversed: the largest pass last)
  *   z_tile:      spectrum columns per z-pass CTA, 16 or 32
- * fwi_plan_create picks {1, 0, 32}.  Setting a schedule keeps the workspace size;
+ *   split_plane: 0 = one CTA transforms a whole z-plane in shared memory; 1 = the XY
+ *                work of a plane is split into column (y) and row-pair (x) passes
+ *                through global memory (always used when a plane does not fit)
+ * fwi_plan_create picks {1, 0, 32, 0} (split_plane = 1 if the plane does not fit).  Setting a schedule keeps the workspace size;
  * it may be changed after binding (between calls).  Results differ only by FP32
  * rounding order.  Errors: FWI_EINVAL (bad values), FWI_ENOTSUP (the shared memory
  * the schedule needs exceeds the device limit).
@@ -166,6 +169,7 @@ typedef struct fwi_schedule {
   int32_t specialized;
   int32_t radix_order;
   int32_t z_tile;
+  int32_t split_plane;
 } fwi_schedule;
 fwi_status fwi_plan_set_schedule(fwi_plan *plan, const fwi_schedule *schedule);
 fwi_status fwi_plan_get_schedule(const fwi_plan *plan, fwi_schedule *schedule);

@@ -17,9 +17,10 @@ import torch
 
 from . import fwi
 
-CANDIDATES = [dict(specialized=s, radix_order=r, z_tile=t)
-              for s in (1, 0) for r in (0, 1, 2) for t in (32, 16)
-              if not (s == 1 and r != 0)]
+CANDIDATES = [dict(specialized=s, radix_order=r, z_tile=t, split_plane=sp)
+              for sp in (0, 1) for s in (1, 0) for r in (0, 1, 2) for t in (32, 16)
+              if not (s == 1 and r != 0) and not (sp == 1 and s == 1)]
+KNOBS = ("specialized", "radix_order", "z_tile", "split_plane")
 
 
 def cache_path() -> str:
@@ -40,14 +41,16 @@ def key_of(nx, ny, nz, K) -> str:
 
 
 def set_schedule(plan, sched: dict) -> int:
-    s = fwi.fwi_schedule(sched["specialized"], sched["radix_order"], sched["z_tile"])
+    s = fwi.fwi_schedule(sched["specialized"], sched["radix_order"], sched["z_tile"],
+                         sched.get("split_plane", 0))
     return fwi.lib().fwi_plan_set_schedule(plan.handle, ctypes.byref(s))
 
 
 def get_schedule(plan) -> dict:
     s = fwi.fwi_schedule()
     fwi._check(fwi.lib().fwi_plan_get_schedule(plan.handle, ctypes.byref(s)), "fwi_plan_get_schedule")
-    return dict(specialized=s.specialized, radix_order=s.radix_order, z_tile=s.z_tile)
+    return dict(specialized=s.specialized, radix_order=s.radix_order, z_tile=s.z_tile,
+                split_plane=s.split_plane)
 
 
 def tune(wl, K: int = 1, steps: int = 24, reps: int = 3, device="cuda", save=True, verbose=False) -> dict:
@@ -81,7 +84,7 @@ def tune(wl, K: int = 1, steps: int = 24, reps: int = 3, device="cuda", save=Tru
             print(cand, f"{best:.3f} ms")
     probe.close()
     win = min(timings, key=lambda t: t["ms"])
-    result = {"schedule": {k: win[k] for k in ("specialized", "radix_order", "z_tile")},
+    result = {"schedule": {k: win[k] for k in KNOBS},
               "ms": win["ms"], "steps": steps, "timings": timings}
     if save:
         path = cache_path()

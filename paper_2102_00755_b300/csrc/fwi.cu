@@ -266,6 +266,8 @@ struct fwi_plan {
   int fxy;   // specialised plane side (0: runtime schedules)
   int fz;    // specialised z length (0: runtime schedules)
   int tz;    // z-pass tile width (columns)
+  int split; // XY work split into column and row-pair passes (large planes)
+  size_t smem_ypass3, smem_ypass1, smem_xmom, smem_xmass;
   fwi_schedule sched;
   // host tables
   std::vector<float2> tw, ap[3], am[3];
@@ -429,8 +431,21 @@ void set_attrs_z(int cap) {
   cudaFuncSetAttribute(k_zpass<0, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_zpass<1, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
+template <int E>
+void set_attrs_split(int cap) {
+  cudaFuncSetAttribute(k_ypass<Y_INV_MOM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_ypass<Y_INV_MASS, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_ypass<Y_FWD3, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_ypass<Y_FWD1, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_xpass_mom<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_xpass_mass<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_xpass_tr_init<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
+
 void set_attrs(fwi_plan* p) {
   const int cap = smem_optin_max();
+  if (p->epl == 8) set_attrs_split<8>(cap);
+  else set_attrs_split<16>(cap);
   PLANE_DISPATCH(p, (set_attrs_plane<E, F>(cap)));
   Z_DISPATCH(p, (set_attrs_z<E, FZ, TZ>(cap)));
   // Touch every small kernel too, so that modules are loaded before any stream
@@ -460,7 +475,44 @@ void prof_end(fwi_plan* p, cudaStream_t st, int slot) {
 }
 
 // One time step for a batch of simulations (four launches).
+template <int EL>
+fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) {
+  const dim3 gz((p->mspec + p->tz - 1) / p->tz, P.nsims);
+  const dim3 gy((p->hx + kTY - 1) / kTY, p->prob.nz, P.nsims);
+  const int g1 = std::max(1, 16 * EL / p->hx), g2 = std::max(1, 8 * EL / p->hx);
+  const int warps = kTpbPlane / 32;
+  const dim3 gx1((p->npair + warps * g1 - 1) / (warps * g1), p->prob.nz, P.nsims);
+  const dim3 gx2((p->npair + warps * g2 - 1) / (warps * g2), p->prob.nz, P.nsims);
+  int slot;
+  prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
+  Z_DISPATCH(p, (k_zpass<0, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+  LAUNCHED("k_zpass<momentum>");
+  prof_end(p, st, slot);
+  prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
+  k_ypass<Y_INV_MOM, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
+  LAUNCHED("k_ypass<inverse, momentum>");
+  k_xpass_mom<EL><<<gx1, kTpbPlane, p->smem_xmom, st>>>(P);
+  LAUNCHED("k_xpass_mom");
+  k_ypass<Y_FWD3, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
+  LAUNCHED("k_ypass<forward x3>");
+  prof_end(p, st, slot);
+  prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
+  Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+  LAUNCHED("k_zpass<mass>");
+  prof_end(p, st, slot);
+  prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
+  k_ypass<Y_INV_MASS, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
+  LAUNCHED("k_ypass<inverse, mass>");
+  k_xpass_mass<EL><<<gx2, kTpbPlane, p->smem_xmass, st>>>(P);
+  LAUNCHED("k_xpass_mass");
+  k_ypass<Y_FWD1, EL><<<gy, kTpbZ, p->smem_ypass1, st>>>(P);
+  LAUNCHED("k_ypass<forward x1>");
+  prof_end(p, st, slot);
+  return FWI_OK;
+}
+
 fwi_status launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) {
+  if (p->split) return p->epl == 8 ? launch_step_split<8>(p, P, st) : launch_step_split<16>(p, P, st);
   const dim3 gz((p->mspec + p->tz - 1) / p->tz, P.nsims);
   const dim3 gp(p->prob.nz, P.nsims);
   int slot;
@@ -512,7 +564,8 @@ fwi_status apply_schedule(fwi_plan* p) {
       if (x == v) return true;
     return false;
   };
-  p->fxy = (sc.specialized && q.nx == q.ny && in(q.nx, {32, 64, 96, 128, 160})) ? q.nx : 0;
+  p->split = sc.split_plane;
+  p->fxy = (!p->split && sc.specialized && q.nx == q.ny && in(q.nx, {32, 64, 96, 128, 160})) ? q.nx : 0;
   p->fz = (sc.specialized && in(q.nz, {32, 48, 64, 80, 96, 128})) ? q.nz : 0;
   p->tz = sc.z_tile;
   const int tw_x = p->ax.tw_off, tw_y = p->ay.tw_off, tw_z = p->az.tw_off;
@@ -529,7 +582,7 @@ fwi_status apply_schedule(fwi_plan* p) {
     if (p->fxy > 0) {
       while (2 * g <= budget / p->fxy) g *= 2;
     } else {
-      g = std::max(1, (budget / 256) * 16 * p->epl / p->hx);
+      g = std::max(1, budget * p->epl / (16 * p->hx));
     }
     return g;
   };
@@ -540,8 +593,18 @@ fwi_status apply_schedule(fwi_plan* p) {
   const size_t ztw = (size_t)((q.nz + 31) & ~31);
   p->smem_zmom = (ztw + (size_t)(2 * p->tz + 4) * q.nz) * sizeof(float2);
   p->smem_zmass = (ztw + (size_t)(3 * p->tz + 4) * q.nz) * sizeof(float2);
-  if (std::max(q.nx, std::max(q.ny, q.nz)) > 512 || p->smem_mass > 227 * 1024 ||
-      p->smem_zmass > 227 * 1024)
+  // split planes: column passes over y and warp-owned row pairs for the x work
+  {
+    const size_t ytw = (size_t)((q.ny + 31) & ~31);
+    p->smem_ypass3 = (ytw + (size_t)(3 * kTY + 4) * q.ny) * sizeof(float2);
+    p->smem_ypass1 = (ytw + (size_t)(1 * kTY + 4) * q.ny) * sizeof(float2);
+    const int g1 = std::max(1, 16 * p->epl / p->hx), g2 = std::max(1, 8 * p->epl / p->hx);
+    const size_t xtw = (size_t)((q.nx + 31) & ~31);
+    p->smem_xmom = (xtw + warps * (size_t)g1 * 2 * p->hx) * sizeof(float2) + warps * 2 * g1 * q.nx * 4;
+    p->smem_xmass = (xtw + warps * (size_t)g2 * 2 * p->hx) * sizeof(float2) + warps * 4 * 2 * g2 * q.nx * 4;
+  }
+  if (std::max(q.nx, std::max(q.ny, q.nz)) > 512 || p->smem_zmass > 227 * 1024) return FWI_ENOTSUP;
+  if (p->split ? (p->smem_ypass3 > 227 * 1024 || p->smem_xmass > 227 * 1024) : p->smem_mass > 227 * 1024)
     return FWI_ENOTSUP;
   return FWI_OK;
 }
@@ -716,10 +779,13 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   }
 
   // launch shapes: every axis must fit one warp group (n <= 512)
-  p->sched = fwi_schedule{1, 0, 32};
+  p->sched = fwi_schedule{1, 0, 32, 0};
   if (apply_schedule(p) != FWI_OK) {
-    delete p;
-    return FWI_ENOTSUP;
+    p->sched.split_plane = 1;            // the plane does not fit one CTA
+    if (apply_schedule(p) != FWI_OK) {
+      delete p;
+      return FWI_ENOTSUP;
+    }
   }
   // workspace layout
   Layout& L = p->L;
@@ -866,8 +932,25 @@ fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32
     T.tidx[k] = 1;
     T.slot[k] = 1;
   }
-  PLANE_DISPATCH(p, (k_tr_init<E, F, F><<<dim3(q.nz, K), kTpbPlane, p->smem_plane, st>>>(T)));
-  LAUNCHED("k_tr_init");
+  if (p->split) {
+    const int warps = kTpbPlane / 32;
+    const dim3 gy((p->hx + kTY - 1) / kTY, q.nz, K);
+    if (p->epl == 8) {
+      const int g = std::max(1, 16 * 8 / p->hx);
+      k_xpass_tr_init<8><<<dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), kTpbPlane, p->smem_xmom, st>>>(T);
+      LAUNCHED("k_xpass_tr_init");
+      k_ypass<Y_FWD1, 8><<<gy, kTpbZ, p->smem_ypass1, st>>>(T);
+    } else {
+      const int g = std::max(1, 16 * 16 / p->hx);
+      k_xpass_tr_init<16><<<dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), kTpbPlane, p->smem_xmom, st>>>(T);
+      LAUNCHED("k_xpass_tr_init");
+      k_ypass<Y_FWD1, 16><<<gy, kTpbZ, p->smem_ypass1, st>>>(T);
+    }
+    LAUNCHED("k_ypass<forward x1>");
+  } else {
+    PLANE_DISPATCH(p, (k_tr_init<E, F, F><<<dim3(q.nz, K), kTpbPlane, p->smem_plane, st>>>(T)));
+    LAUNCHED("k_tr_init");
+  }
   if ((s = launch_step(p, T, st)) != FWI_OK) return s;
   // interleaved adjoint and TR iterations
   const bool exact = q.pairing == FWI_PAIRING_EXACT;
@@ -1132,7 +1215,7 @@ fwi_status fwi_batch_destroy(fwi_batch* b) {
 fwi_status fwi_plan_set_schedule(fwi_plan* p, const fwi_schedule* sc) {
   if (!p || !sc) return FWI_EINVAL;
   if ((sc->specialized != 0 && sc->specialized != 1) || sc->radix_order < 0 || sc->radix_order > 2 ||
-      (sc->z_tile != 16 && sc->z_tile != 32))
+      (sc->z_tile != 16 && sc->z_tile != 32) || (sc->split_plane != 0 && sc->split_plane != 1))
     return FWI_EINVAL;
   const fwi_schedule old = p->sched;
   p->sched = *sc;

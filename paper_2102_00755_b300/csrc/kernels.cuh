@@ -220,10 +220,11 @@ struct PlaneCfg {
   static constexpr int GXc = FX > 0 ? pow2_floor(XW / FX) : 0;
   static constexpr int GYc = FY > 0 ? pow2_floor(256 / FY) : 0;
   static constexpr int PI = FX > 0 ? (GXc * FX + 31) / 32 : EPL;
-  static constexpr int UI = FX > 0 ? (GXc * (FX / 2 + 1) + 31) / 32 : EPL / 2;
+  // runtime path: a lone line of nx = 32 EPL has hx = 16 EPL + 1 bins
+  static constexpr int UI = FX > 0 ? (GXc * (FX / 2 + 1) + 31) / 32 : EPL / 2 + 1;
   __device__ static int gx(const StepParams& P) {
     if (FX > 0) return GXc;
-    const int g = (XW / 256) * 16 * EPL / P.hx;   // group * 2 hx <= 32 EPL
+    const int g = XW * EPL / (16 * P.hx);   // group * 2 hx <= XW EPL / 8 <= 32 EPL
     return g < 1 ? 1 : g;
   }
   __device__ static int gy(const StepParams& P) { return FY > 0 ? GYc : lines_per_group<EPL>(P.ny); }
@@ -610,6 +611,340 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_tr_init(const __grid_constant_
   }
   __syncthreads();
   forward_y_and_store<C>(sm, twy, P, S.spec[0] + (size_t)z * P.mspec);
+}
+
+}  // namespace fwi
+
+namespace fwi {
+
+// ======================================================================= split planes
+// Planes too large for one CTA's shared memory run each XY half-step as
+//   k_ypass (columns: y transforms of TY adjacent kx columns of one z-plane) and
+//   k_xpass (warps own pair lines of one z-plane: C2R, x transforms, field update,
+//            sparse work, R2C; rows are read from and written back to global memory).
+// Per step: zpass<MOM>, ypass<INV_MOM>, xpass<MOM>, ypass<FWD3>, zpass<MASS>,
+// ypass<INV_MASS>, xpass<MASS>, ypass<FWD1>.
+
+enum YKind : int { Y_INV_MOM = 0, Y_INV_MASS = 1, Y_FWD3 = 2, Y_FWD1 = 3 };
+constexpr int kTY = 16;
+
+// Y_INV_MOM:  spec[0] = Q, spec[1] = R  ->  spec[2] = IFFT_y(Q) (x factor applied later),
+//             spec[0] = IFFT_y(a+_y Q), spec[1] = IFFT_y(R)
+// Y_INV_MASS: spec[2], spec[0] (times a-_y), spec[1]: inverse y, in place
+// Y_FWD3:     spec[2], spec[0], spec[1]: forward y, in place
+// Y_FWD1:     spec[0]: forward y, in place
+template <int KIND, int EPL>
+__global__ void __launch_bounds__(kTpbZ, 2) k_ypass(const __grid_constant__ StepParams P) {
+  if (*P.bad) return;
+  extern __shared__ float2 ysm_raw[];
+  const SimPtrs& S = P.sims[blockIdx.z];
+  constexpr int NSL = KIND == Y_FWD1 ? 1 : 3;
+  constexpr int RS = NSL * kTY + 4;
+  constexpr bool INV = KIND == Y_INV_MOM || KIND == Y_INV_MASS;
+  const int ny = P.ny, hx = P.hx;
+  float2* twy = ysm_raw;
+  for (int i = threadIdx.x; i < ny; i += blockDim.x) twy[i] = P.tw[P.ay.tw_off + i];
+  float2* sm = ysm_raw + ((ny + 31) & ~31);
+  const int k0 = blockIdx.x * kTY;
+  const size_t zoff = (size_t)blockIdx.y * P.mspec;
+  auto src_of = [&](int s) -> float2* {
+    if (KIND == Y_INV_MOM) return s == 2 ? S.spec[1] : S.spec[0];
+    if (KIND == Y_FWD1) return S.spec[0];
+    return s == 0 ? S.spec[2] : (s == 1 ? S.spec[0] : S.spec[1]);
+  };
+  auto dst_of = [&](int s) -> float2* {
+    if (KIND == Y_INV_MOM) return s == 0 ? S.spec[2] : (s == 1 ? S.spec[0] : S.spec[1]);
+    return src_of(s);
+  };
+  for (int idx = threadIdx.x; idx < NSL * ny * kTY; idx += blockDim.x) {
+    const int ml = idx % kTY;
+    const int t = idx / kTY;
+    const int s = t / ny;
+    const int y = t - s * ny;
+    const int kx = k0 + ml;
+    if (kx < hx) cp_async8(&sm[y * RS + s * kTY + ml], &src_of(s)[zoff + (size_t)y * hx + kx]);
+    else sm[y * RS + s * kTY + ml] = make_float2(0.f, 0.f);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (KIND == Y_INV_MOM || KIND == Y_INV_MASS) {   // y factor on the y component's slot
+    for (int idx = threadIdx.x; idx < ny * kTY; idx += blockDim.x) {
+      const int ml = idx % kTY;
+      const int y = idx / kTY;
+      const float2 f = KIND == Y_INV_MOM ? __ldg(&P.ap[1][y]) : __ldg(&P.am[1][y]);
+      sm[y * RS + 1 * kTY + ml] = cmul(sm[y * RS + 1 * kTY + ml], f);
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = min(lines_per_group<EPL>(ny), kTY);
+  const int gps = (kTY + G - 1) / G;
+  for (int g = warp; g < NSL * gps; g += nw) {
+    const int s = g / gps;
+    const int c0 = (g - s * gps) * G;
+    warp_fft<INV, EPL>(sm + s * kTY + c0, min(G, kTY - c0), 1, RS, P.ay, twy, lane);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < NSL * ny * kTY; idx += blockDim.x) {
+    const int ml = idx % kTY;
+    const int t = idx / kTY;
+    const int s = t / ny;
+    const int y = t - s * ny;
+    const int kx = k0 + ml;
+    if (kx < hx) dst_of(s)[zoff + (size_t)y * hx + kx] = sm[y * RS + s * kTY + ml];
+  }
+}
+
+// Rows 2p, 2p+1 of a y-transformed spectrum plane -> the warp's pair-line region
+// (asynchronous; the missing row of an odd ny is zero).
+__device__ __forceinline__ void warp_load_pairs(float2* reg, const float2* __restrict__ plane, int p0,
+                                                int nl, int hx, int ny, int lane) {
+  const int rows = min(2 * nl, ny - 2 * p0);
+  const int tot = rows * hx;
+  const float2* src = plane + (size_t)(2 * p0) * hx;
+  for (int i = lane; i < tot; i += 32) cp_async8(&reg[i], &src[i]);
+  for (int i = tot + lane; i < 2 * nl * hx; i += 32) reg[i] = make_float2(0.f, 0.f);
+}
+__device__ __forceinline__ void warp_store_pairs(const float2* reg, float2* __restrict__ plane, int p0,
+                                                 int nl, int hx, int ny, int lane) {
+  const int rows = min(2 * nl, ny - 2 * p0);
+  float2* dst = plane + (size_t)(2 * p0) * hx;
+  for (int i = lane; i < rows * hx; i += 32) dst[i] = reg[i];
+}
+
+// x work of the momentum half-step on split planes (see k_plane_mom).
+template <int EPL>
+__global__ void __launch_bounds__(kTpbPlane, 2) k_xpass_mom(const __grid_constant__ StepParams P) {
+  if (*P.bad) return;
+  using C = PlaneCfg<EPL, 0, 0>;
+  extern __shared__ float2 xsm_raw[];
+  const float2* twx = xsm_raw;
+  const int nx = P.nx, ny = P.ny, hx = P.hx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) xsm_raw[i] = P.tw[P.ax.tw_off + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = C::gx(P);
+  float2* reg = xsm_raw + ((nx + 31) & ~31) + warp * G * 2 * hx;
+  float* stage = reinterpret_cast<float*>(xsm_raw + ((nx + 31) & ~31) + nw * G * 2 * hx) + warp * 2 * G * nx;
+  const int z = blockIdx.y;
+  const SimPtrs& S = P.sims[blockIdx.z];
+  const size_t soff = (size_t)z * P.mspec;
+  const size_t voff = (size_t)z * P.plane;
+  const int p0 = (blockIdx.x * nw + warp) * G;
+  if (p0 >= P.npair) return;
+  const int nl = min(G, P.npair - p0);
+  // component z (spec[1]), x (spec[2] = IFFT_y(Q), times a+_x here), y (spec[0])
+  for (int cc = 0; cc < 3; ++cc) {
+    const int comp = cc == 0 ? 2 : cc - 1;
+    float2* buf = (comp == 2 ? S.spec[1] : (comp == 0 ? S.spec[2] : S.spec[0])) + soff;
+    float* v = S.v[comp] + voff;
+    warp_load_pairs(reg, buf, p0, nl, hx, ny, lane);
+    warp_prefetch_rows(stage, v, p0, nl, nx, ny, lane);
+    cp_async_wait_all();
+    __syncwarp();
+    if (comp == 0) {
+      for (int i = lane; i < nl * 2 * hx; i += 32) reg[i] = cmul(reg[i], __ldg(&P.ap[0][i % hx]));
+      __syncwarp();
+    }
+    warp_c2r_pack<C::PI>(reg, nl, nx, hx, ny, p0, lane);
+    C::template fft_x<true>(reg, nl, P, twx, lane);
+    const float* lam = P.lams[comp];
+    const float lz = __ldg(&lam[comp == 2 ? z : 0]);
+    for (int l = 0; l < nl; ++l) {
+      const int y0 = 2 * (p0 + l), y1 = y0 + 1;
+      float2* Z = reg + l * 2 * hx;
+      const float* s0 = stage + (2 * l) * nx;
+      for (int x = lane; x < nx; x += 32) {
+        const float2 d = Z[x];
+        float l0, l1;
+        if (comp == 0) { l0 = l1 = __ldg(&lam[x]); }
+        else if (comp == 1) { l0 = __ldg(&lam[y0]); l1 = (y1 < ny) ? __ldg(&lam[y1]) : 1.f; }
+        else { l0 = l1 = lz; }
+        const float v0 = l0 * (l0 * s0[x] - P.dt_over_rho0 * d.x);
+        v[y0 * nx + x] = v0;
+        float v1 = 0.f;
+        if (y1 < ny) {
+          v1 = l1 * (l1 * s0[nx + x] - P.dt_over_rho0 * d.y);
+          v[y1 * nx + x] = v1;
+        }
+        Z[x] = make_float2(v0, v1);
+      }
+    }
+    __syncwarp();
+    C::template fft_x<false>(reg, nl, P, twx, lane);
+    warp_r2c_unpack<C::UI>(reg, nl, nx, hx, ny, p0, lane);
+    warp_store_pairs(reg, buf, p0, nl, hx, ny, lane);
+    __syncwarp();
+  }
+}
+
+// x work of the mass half-step on split planes (see k_plane_mass); writes the
+// x-transformed p rows into spec[0] (the y transform follows in k_ypass<Y_FWD1>).
+template <int EPL>
+__global__ void __launch_bounds__(kTpbPlane, 2) k_xpass_mass(const __grid_constant__ StepParams P) {
+  if (*P.bad) return;
+  using C = PlaneCfg<EPL, 0, 0, 128>;
+  extern __shared__ float2 xsm_raw[];
+  const float2* twx = xsm_raw;
+  const int nx = P.nx, ny = P.ny, hx = P.hx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) xsm_raw[i] = P.tw[P.ax.tw_off + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = C::gx(P);
+  const int stage_n = 2 * G * nx;
+  float2* reg = xsm_raw + ((nx + 31) & ~31) + warp * G * 2 * hx;
+  float* stage = reinterpret_cast<float*>(xsm_raw + ((nx + 31) & ~31) + nw * G * 2 * hx) + warp * 4 * stage_n;
+  const int z = blockIdx.y;
+  const SimPtrs& S = P.sims[blockIdx.z];
+  const int role = S.role, shot = S.shot, tix = P.tidx[blockIdx.z];
+  const size_t soff = (size_t)z * P.mspec;
+  const size_t voff = (size_t)z * P.plane;
+  const int p0 = (blockIdx.x * nw + warp) * G;
+  if (p0 >= P.npair) return;
+  const int nl = min(G, P.npair - p0);
+  const float* c2 = P.c2 + voff;
+  const float* rx = S.rho[0] + voff;
+  const float* rz = S.rho[2] + voff;
+  for (int cc = 0; cc < 3; ++cc) {
+    const int comp = cc == 0 ? 0 : (cc == 1 ? 2 : 1);
+    float2* buf = (comp == 0 ? S.spec[2] : (comp == 2 ? S.spec[1] : S.spec[0])) + soff;
+    float* rho = S.rho[comp] + voff;
+    warp_load_pairs(reg, buf, p0, nl, hx, ny, lane);
+    warp_prefetch_rows(stage, rho, p0, nl, nx, ny, lane);
+    if (cc == 2) {
+      warp_prefetch_rows(stage + stage_n, rx, p0, nl, nx, ny, lane);
+      warp_prefetch_rows(stage + 2 * stage_n, rz, p0, nl, nx, ny, lane);
+      warp_prefetch_rows(stage + 3 * stage_n, c2, p0, nl, nx, ny, lane);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    if (comp == 0) {
+      for (int i = lane; i < nl * 2 * hx; i += 32) reg[i] = cmul(reg[i], __ldg(&P.am[0][i % hx]));
+      __syncwarp();
+    }
+    warp_c2r_pack<C::PI>(reg, nl, nx, hx, ny, p0, lane);
+    C::template fft_x<true>(reg, nl, P, twx, lane);
+    const float* lam = P.lam[comp];
+    const float lz = __ldg(&lam[comp == 2 ? z : 0]);
+    for (int l = 0; l < nl; ++l) {
+      const int y0 = 2 * (p0 + l), y1 = y0 + 1;
+      float2* Z = reg + l * 2 * hx;
+      const int o0 = (2 * l) * nx, o1 = o0 + nx;
+      for (int x = lane; x < nx; x += 32) {
+        const float2 d = Z[x];
+        float l0, l1;
+        if (comp == 0) { l0 = l1 = __ldg(&lam[x]); }
+        else if (comp == 1) { l0 = __ldg(&lam[y0]); l1 = (y1 < ny) ? __ldg(&lam[y1]) : 1.f; }
+        else { l0 = l1 = lz; }
+        const int i0 = y0 * nx + x, i1 = y1 * nx + x;
+        const float r0 = l0 * (l0 * stage[o0 + x] - P.dt_rho0 * d.x);
+        rho[i0] = r0;
+        float r1 = 0.f;
+        if (y1 < ny) {
+          r1 = l1 * (l1 * stage[o1 + x] - P.dt_rho0 * d.y);
+          rho[i1] = r1;
+        }
+        if (cc == 2) {
+          const float* sx = stage + stage_n;
+          const float* sz = stage + 2 * stage_n;
+          const float* sc = stage + 3 * stage_n;
+          const float p0v = sc[o0 + x] * (sx[o0 + x] + r0 + sz[o0 + x]);
+          const float p1v = (y1 < ny) ? sc[o1 + x] * (sx[o1 + x] + r1 + sz[o1 + x]) : 0.f;
+          Z[x] = make_float2(p0v, p1v);
+        }
+      }
+    }
+    __syncwarp();
+    if (cc < 2) continue;
+    // sparse updates of rho_xi and p on these pair lines, then recording (offsets
+    // pf are relative to the plane buffer; this warp's region starts at pair p0)
+    const int key0 = z * P.npair + p0;
+    float* zf = reinterpret_cast<float*>(reg) - 4 * hx * p0;
+    if (role == ROLE_FORWARD) {
+      const float* amp = P.amp_src + ((size_t)shot * P.nt + tix) * P.n_us;
+      for (int u = P.us_ptr[key0] + lane; u < P.us_ptr[key0 + nl]; u += 32) {
+        const int vx = P.us_vox[u];
+        const float a = amp[u];
+        S.rho[0][vx] += a;
+        S.rho[1][vx] += a;
+        S.rho[2][vx] += a;
+        zf[P.us_pf[u]] += P.c2[vx] * (3.f * a);
+      }
+    } else if (role == ROLE_ADJOINT) {
+      const float* q = P.qf + ((size_t)shot * P.nt + tix) * P.n_rec;
+      for (int u = P.ur_ptr[key0] + lane; u < P.ur_ptr[key0 + nl]; u += 32) {
+        float s = 0.f;
+        for (int e = P.ur_mptr[u]; e < P.ur_mptr[u + 1]; ++e) s += q[P.ur_mem[e]];
+        const float a = P.ur_coef[u] * s;
+        const int vx = P.ur_vox[u];
+        S.rho[0][vx] += a;
+        S.rho[1][vx] += a;
+        S.rho[2][vx] += a;
+        zf[P.ur_pf[u]] += P.c2[vx] * (3.f * a);
+      }
+    } else {
+      const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1 - tix)) * P.n_layer;
+      for (int j = P.lay_ptr[key0] + lane; j < P.lay_ptr[key0 + nl]; j += 32) {
+        const int vx = P.lay_vox[j];
+        const float val = g[j] * P.inv3c2[j];
+        S.rho[0][vx] = val;
+        S.rho[1][vx] = val;
+        S.rho[2][vx] = val;
+        zf[P.lay_pf[j]] = P.c2[vx] * (3.f * val);
+      }
+    }
+    __syncwarp();
+    if (role == ROLE_FORWARD) {
+      float* f = P.traces + ((size_t)shot * P.nt + tix) * P.n_rec;
+      for (int e = P.rr_ptr[key0] + lane; e < P.rr_ptr[key0 + nl]; e += 32) f[P.rr_col[e]] = zf[P.rr_pf[e]];
+      if (P.record_layer) {
+        float* g = P.ghist + ((size_t)shot * P.nt + tix) * P.n_layer;
+        for (int j = P.lay_ptr[key0] + lane; j < P.lay_ptr[key0 + nl]; j += 32) g[j] = zf[P.lay_pf[j]];
+      }
+    } else {
+      float* out = role == ROLE_ADJOINT ? P.pa + (size_t)shot * P.n_gamma
+                                        : P.ring + ((size_t)shot * 3 + P.slot[blockIdx.z]) * P.n_gamma;
+      for (int j = P.gam_ptr[key0] + lane; j < P.gam_ptr[key0 + nl]; j += 32) out[j] = zf[P.gam_pf[j]];
+    }
+    __syncwarp();
+    C::template fft_x<false>(reg, nl, P, twx, lane);
+    warp_r2c_unpack<C::UI>(reg, nl, nx, hx, ny, p0, lane);
+    warp_store_pairs(reg, S.spec[0] + soff, p0, nl, hx, ny, lane);
+  }
+}
+
+// TR initial value on split planes: x work only (k_ypass<Y_FWD1> follows).
+template <int EPL>
+__global__ void __launch_bounds__(kTpbPlane, 2) k_xpass_tr_init(const __grid_constant__ StepParams P) {
+  if (*P.bad) return;
+  using C = PlaneCfg<EPL, 0, 0>;
+  extern __shared__ float2 xsm_raw[];
+  const float2* twx = xsm_raw;
+  const int nx = P.nx, ny = P.ny, hx = P.hx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) xsm_raw[i] = P.tw[P.ax.tw_off + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = C::gx(P);
+  float2* reg = xsm_raw + ((nx + 31) & ~31) + warp * G * 2 * hx;
+  const int z = blockIdx.y;
+  const SimPtrs& S = P.sims[blockIdx.z];
+  const int shot = S.shot;
+  const int p0 = (blockIdx.x * nw + warp) * G;
+  if (p0 >= P.npair) return;
+  const int nl = min(G, P.npair - p0);
+  for (int i = lane; i < nl * 2 * hx; i += 32) reg[i] = make_float2(0.f, 0.f);
+  __syncwarp();
+  const int key0 = z * P.npair + p0;
+  float* zf = reinterpret_cast<float*>(reg) - 4 * hx * p0;
+  const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1)) * P.n_layer;
+  for (int j = P.lay_ptr[key0] + lane; j < P.lay_ptr[key0 + nl]; j += 32) zf[P.lay_pf[j]] = g[j];
+  __syncwarp();
+  float* out = P.ring + ((size_t)shot * 3 + 0) * P.n_gamma;
+  for (int j = P.gam_ptr[key0] + lane; j < P.gam_ptr[key0 + nl]; j += 32) out[j] = zf[P.gam_pf[j]];
+  __syncwarp();
+  C::template fft_x<false>(reg, nl, P, twx, lane);
+  warp_r2c_unpack<C::UI>(reg, nl, nx, hx, ny, p0, lane);
+  warp_store_pairs(reg, S.spec[0] + (size_t)z * P.mspec, p0, nl, hx, ny, lane);
 }
 
 }  // namespace fwi

@@ -50,7 +50,8 @@ class FwiError(RuntimeError):
 
 
 class fwi_schedule(ctypes.Structure):
-    _fields_ = [("specialized", ctypes.c_int32), ("radix_order", ctypes.c_int32), ("z_tile", ctypes.c_int32)]
+    _fields_ = [("specialized", ctypes.c_int32), ("radix_order", ctypes.c_int32), ("z_tile", ctypes.c_int32),
+                ("split_plane", ctypes.c_int32)]
 
 
 class fwi_problem(ctypes.Structure):
