@@ -239,6 +239,63 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serve(args):
+    """Serving: a seeded Poisson stream of forward and gradient requests over the three
+    multigrid levels (135x135x96 / 243x243x135 / 480x480x256 with PML; 1000 / 2000 / 4000
+    steps; 1024 receivers; 2..8 encoded emitters out of 8), level mix 128:128:32, half
+    gradients, served by the continuous-batching server (admission by free HBM)."""
+    import torch
+
+    from paper_2102_00755_b300 import fwi, serve, synth
+
+    dev = torch.device("cuda", 0)
+    names, levels, t_data = [], [], {}
+    for L in range(3):
+        wl = synth.serving_level(L, n_src=8, seed=1000 + L)
+        if args.nt:
+            nt = max(8, int(args.nt * wl.nt / synth.SERVING_LEVELS[2][2]))
+            wl.nt, wl.wavelet = nt, wl.wavelet[:nt]
+        t0 = time.perf_counter()
+        levels.append(serve.make_level(f"L{L}", wl, device=dev))
+        t_data[f"L{L}"] = time.perf_counter() - t0
+        names.append(f"L{L}")
+    server = serve.Server(levels, device=dev, max_inflight=args.inflight)
+    # warm the two smaller levels (module loading, first uncaptured call, graph capture)
+    warm = [serve.Request(-1 - i, nm, kind, np.eye(8)[0], 0.0)
+            for i, (nm, kind) in enumerate([(n, k) for n in names[:2] for k in ("forward", "gradient")] * 2)]
+    server.run(warm, realtime=False)
+    reqs = serve.poisson_stream(names, [128, 128, 32], args.requests, args.rate, 8, seed=1000)
+    with ClockSampler(0) as clk:
+        out = server.run(reqs, realtime=True)
+    stats = out["stats"]
+    res = out["results"]
+    assert all(p.status() == fwi.FWI_OK for slots in server.pool.values() for p in [s.plan for s in slots])
+    per = {}
+    for nm in names:
+        for kind in ("forward", "gradient"):
+            lat = [r.latency for r in res if r.level == nm and r.kind == kind]
+            svc = [r.done - r.admitted for r in res if r.level == nm and r.kind == kind]
+            if lat:
+                per[f"{nm}-{kind}"] = {"n": len(lat), "p50_s": float(np.percentile(lat, 50)),
+                                       "p99_s": float(np.percentile(lat, 99)),
+                                       "median_in_service_s": float(np.median(svc))}
+    grid = {nm: [lv.wl.nx, lv.wl.ny, lv.wl.nz, lv.wl.nt] for nm, lv in zip(names, levels)}
+    line = {"metric": METRIC, "value": stats["gvoxel_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": len(res), "warmup": len(warm), "ms_per_step": 1e3 * stats["wall_s"] / max(len(res), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": "serving: Poisson stream of forward/gradient requests over multigrid "
+                                   "levels 135x135x96, 243x243x135, 480x480x256 (PML incl.)",
+                       "levels": grid, "requests": args.requests, "rate_req_per_s": args.rate,
+                       "level_mix": [128, 128, 32], "p_gradient": 0.5, "emitters_per_request": "2..8",
+                       "max_inflight": args.inflight, "raw_data_generation_s": t_data},
+            "latency_s": {"p50": stats["p50_s"], "p99": stats["p99_s"]},
+            "gradients_per_h": stats["gradients_per_h"], "serve_stats": stats, "per_level": per,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    server.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,15 +307,22 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--nt", type=int, default=0,
                     help="override the number of time samples (small profiling cases only)")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch"],
+    ap.add_argument("--requests", type=int, default=64, help="serve: length of the request stream")
+    ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrival rate (requests/s)")
+    ap.add_argument("--inflight", type=int, default=8, help="serve: admitted requests at most")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve"],
                     help="plain: the 128x128x64 gradient (the reported line); batch: the 16-instance "
-                         "uneven-grid configuration as one captured graph vs sequential forms")
+                         "uneven-grid configuration as one captured graph vs sequential forms; "
+                         "serve: the Poisson request stream over the three multigrid levels")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
 
     import torch

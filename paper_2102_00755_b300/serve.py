@@ -259,7 +259,10 @@ def make_level(name, wl, device="cuda") -> Level:
     c_true = torch.tensor(wl.c_true, dtype=torch.float32, device=dev).reshape(-1)
     c = torch.tensor(wl.c_model, dtype=torch.float32, device=dev).reshape(-1)
     n_src = len(wl.src_idx)
-    plan = fwi.Plan.from_workload(wl, max_shots=min(n_src, 8), device=dev)
+    # forward only: no boundary-layer history is recorded, so the plan gets one-voxel
+    # Gamma and layer lists instead of reserving K * nt * |layer| floats
+    fwd = dataclasses.replace(wl, layer_idx=wl.layer_idx[:1], gamma_idx=wl.gamma_idx[:1])
+    plan = fwi.Plan.from_workload(fwd, max_shots=min(n_src, 8), device=dev)
     raw = torch.empty((n_src, wl.nt, len(wl.rec_idx)), dtype=torch.float32, device=dev)
     for s0 in range(0, n_src, 8):
         k = min(8, n_src - s0)
@@ -268,6 +271,8 @@ def make_level(name, wl, device="cuda") -> Level:
         plan.forward(c_true, w, raw[s0:s0 + k])
     torch.cuda.synchronize(dev)
     plan.close()
+    del plan
+    torch.cuda.empty_cache()
     return Level(name, wl, c, raw)
 
 

@@ -431,3 +431,24 @@ def test_paper_grid_and_pml_rule():
         tot = m + 2 * P
         for p in (7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47):
             assert tot % p != 0
+
+
+# ---------------------------------------------------------------------------
+# Closed-form traces used for full-size parity (App. B, homogeneous medium)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,c", [((12, 10, 9), 1800.0), ((9, 15, 8), 1500.0), ((16, 16, 12), 1800.0)])
+def test_closed_form_traces_match_time_stepping(shape, c):
+    """The per-mode recurrence summed at receiver offsets (half spectrum in x, with
+    wrap-around offsets) equals the oracle's time-stepping forward traces."""
+    from oracle import closed_form
+    nx, ny, nz = shape
+    G = _grid(nx, ny, nz)
+    nt = 60
+    rng = np.random.default_rng(5)
+    src = int(rng.integers(0, nx * ny * nz))
+    rec = rng.choice(nx * ny * nz, size=7, replace=False)
+    s = synth.ricker(nt, G.dt, 0.3e6)
+    f, _ = pstd.forward(G, np.full(G.shape, c), np.array([src]), [1.0], s, rec)
+    cf = closed_form.homogeneous_traces(shape, G.dx, G.dt, C_REF, c, src, rec, s, nt)
+    assert np.abs(f).max() > 0
+    assert np.abs(cf - f).max() < 1e-11 * np.abs(f).max()
