@@ -24,15 +24,15 @@ struct AxisPlan {
   int tw_off;               // offset of this axis' W table in the twiddle array
 };
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // multiply by -i (forward) or +i (inverse)
 template <bool INV>
-__device__ __forceinline__ float2 mul_mi(float2 a) {
+__host__ __device__ __forceinline__ float2 mul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
@@ -42,7 +42,7 @@ struct Dft;
 
 template <bool INV>
 struct Dft<2, INV> {
-  __device__ __forceinline__ static void run(float2* v) {
+  __host__ __device__ __forceinline__ static void run(float2* v) {
     float2 a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
@@ -51,7 +51,7 @@ struct Dft<2, INV> {
 
 template <bool INV>
 struct Dft<4, INV> {
-  __device__ __forceinline__ static void run(float2* v) {
+  __host__ __device__ __forceinline__ static void run(float2* v) {
     float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
     float2 t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
     v[0] = cadd(t0, t2);
@@ -63,7 +63,7 @@ struct Dft<4, INV> {
 
 template <bool INV>
 struct Dft<3, INV> {
-  __device__ __forceinline__ static void run(float2* v) {
+  __host__ __device__ __forceinline__ static void run(float2* v) {
     const float s1 = 0.86602540378443864676f;  // sin(2 pi / 3)
     float2 t = cadd(v[1], v[2]);
     float2 u = csub(v[1], v[2]);
@@ -77,7 +77,7 @@ struct Dft<3, INV> {
 
 template <bool INV>
 struct Dft<5, INV> {
-  __device__ __forceinline__ static void run(float2* v) {
+  __host__ __device__ __forceinline__ static void run(float2* v) {
     const float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
     const float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
     const float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
@@ -101,7 +101,7 @@ template <bool INV>
 struct Dft<8, INV> {
   // split into even/odd outputs: u_r = a_r + a_(r+4), w_r = (a_r - a_(r+4)) W8^r,
   // y_(2k) = DFT4(u)_k, y_(2k+1) = DFT4(w)_k
-  __device__ __forceinline__ static void run(float2* v) {
+  __host__ __device__ __forceinline__ static void run(float2* v) {
     const float h = 0.70710678118654752440f;
     float2 u[4], w[4];
 #pragma unroll

@@ -14,6 +14,7 @@
 
 #include "../../include/fwi.h"
 #include "kernels.cuh"
+#include "plane2.cuh"
 
 using namespace fwi;
 
@@ -264,6 +265,8 @@ struct fwi_plan {
   size_t smem_plane, smem_mass, smem_zmom, smem_zmass;
   int epl;   // values staged per lane in the runtime warp FFT passes (8 or 16)
   int fxy;   // specialised plane side (0: runtime schedules)
+  int p2;    // plane side of the two-step register-transform plane kernels (0: not used)
+  size_t smem_p2;
   int fz;    // specialised z length (0: runtime schedules)
   int tz;    // z-pass tile width (columns)
   int split; // XY work split into column and row-pair passes (large planes)
@@ -393,6 +396,17 @@ fwi_status cuda_fail(cudaError_t e, const char* what) {
       if ((p)->epl == 8) { constexpr int E = 8, F = 0; CALL; }          \
       else { constexpr int E = 16, F = 0; CALL; }                       \
   }
+// Two-step register-transform plane kernels: square planes of these sides.
+#define P2_DISPATCH(p, CALL)                                            \
+  switch ((p)->p2) {                                                    \
+    case 32: { constexpr int N = 32; CALL; } break;                     \
+    case 64: { constexpr int N = 64; CALL; } break;                     \
+    case 96: { constexpr int N = 96; CALL; } break;                     \
+    case 128: { constexpr int N = 128; CALL; } break;                   \
+    case 135: { constexpr int N = 135; CALL; } break;                   \
+    case 160: { constexpr int N = 160; CALL; } break;                   \
+    default: break;                                                     \
+  }
 #define Z_DISPATCH_T(p, TZ, CALL)                                       \
   switch ((p)->fz) {                                                    \
     case 32: { constexpr int E = 8, FZ = 32; CALL; } break;             \
@@ -426,6 +440,11 @@ void set_attrs_plane(int cap) {
   cudaFuncSetAttribute(k_plane_mass<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_tr_init<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
+template <int N>
+void set_attrs_p2(int cap) {
+  cudaFuncSetAttribute(k_plane2_mom<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_plane2_mass<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
 template <int E, int FZ, int TZ>
 void set_attrs_z(int cap) {
   cudaFuncSetAttribute(k_zpass<0, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
@@ -447,6 +466,7 @@ void set_attrs(fwi_plan* p) {
   if (p->epl == 8) set_attrs_split<8>(cap);
   else set_attrs_split<16>(cap);
   PLANE_DISPATCH(p, (set_attrs_plane<E, F>(cap)));
+  P2_DISPATCH(p, (set_attrs_p2<N>(cap)));
   Z_DISPATCH(p, (set_attrs_z<E, FZ, TZ>(cap)));
   // Touch every small kernel too, so that modules are loaded before any stream
   // capture of a call (a first launch inside a capture may not load them).
@@ -521,16 +541,26 @@ fwi_status launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   LAUNCHED("k_zpass<momentum>");
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
-  PLANE_DISPATCH(p, (k_plane_mom<E, F, F><<<gp, kTpbPlane, p->smem_plane, st>>>(P)));
-  LAUNCHED("k_plane_mom");
+  if (p->p2) {
+    P2_DISPATCH(p, (k_plane2_mom<N, N><<<gp, Plane2<N, N>::NT, p->smem_p2, st>>>(P)));
+    LAUNCHED("k_plane2_mom");
+  } else {
+    PLANE_DISPATCH(p, (k_plane_mom<E, F, F><<<gp, kTpbPlane, p->smem_plane, st>>>(P)));
+    LAUNCHED("k_plane_mom");
+  }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
   Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
   LAUNCHED("k_zpass<mass>");
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
-  PLANE_DISPATCH(p, (k_plane_mass<E, F, F><<<gp, kTpbPlane, p->smem_mass, st>>>(P)));
-  LAUNCHED("k_plane_mass");
+  if (p->p2) {
+    P2_DISPATCH(p, (k_plane2_mass<N, N><<<gp, Plane2<N, N>::NT, p->smem_p2, st>>>(P)));
+    LAUNCHED("k_plane2_mass");
+  } else {
+    PLANE_DISPATCH(p, (k_plane_mass<E, F, F><<<gp, kTpbPlane, p->smem_mass, st>>>(P)));
+    LAUNCHED("k_plane_mass");
+  }
   prof_end(p, st, slot);
   return FWI_OK;
 }
@@ -567,6 +597,14 @@ fwi_status apply_schedule(fwi_plan* p) {
   p->split = sc.split_plane;
   p->fxy = (!p->split && sc.specialized && q.nx == q.ny && in(q.nx, {32, 64, 96, 128, 160})) ? q.nx : 0;
   p->fz = (sc.specialized && in(q.nz, {32, 48, 64, 80, 96, 128})) ? q.nz : 0;
+  p->p2 = 0;
+  p->smem_p2 = 0;
+  if (sc.specialized == 2) {
+    if (p->split || q.nx != q.ny || !in(q.nx, {32, 64, 96, 128, 135, 160})) return FWI_ENOTSUP;
+    p->p2 = q.nx;
+    P2_DISPATCH(p, (p->smem_p2 = Plane2<N, N>::SMEM));
+    if (p->smem_p2 > 227 * 1024) return FWI_ENOTSUP;
+  }
   p->tz = sc.z_tile;
   const int tw_x = p->ax.tw_off, tw_y = p->ay.tw_off, tw_z = p->az.tw_off;
   if (!factor235(q.nx, &p->ax, sc.radix_order) || !factor235(q.ny, &p->ay, sc.radix_order) ||
@@ -779,13 +817,19 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   }
 
   // launch shapes: every axis must fit one warp group (n <= 512)
-  p->sched = fwi_schedule{1, 0, 32, 0};
-  if (apply_schedule(p) != FWI_OK) {
-    p->sched.split_plane = 1;            // the plane does not fit one CTA
-    if (apply_schedule(p) != FWI_OK) {
-      delete p;
-      return FWI_ENOTSUP;
+  // default schedule: two-step plane kernels where built, else the compile-time or
+  // runtime transforms, else (the plane does not fit one CTA) the split planes
+  bool placed = false;
+  for (const fwi_schedule sc : {fwi_schedule{2, 0, 32, 0}, fwi_schedule{1, 0, 32, 0}, fwi_schedule{1, 0, 32, 1}}) {
+    p->sched = sc;
+    if (apply_schedule(p) == FWI_OK) {
+      placed = true;
+      break;
     }
+  }
+  if (!placed) {
+    delete p;
+    return FWI_ENOTSUP;
   }
   // workspace layout
   Layout& L = p->L;
@@ -1214,7 +1258,7 @@ fwi_status fwi_batch_destroy(fwi_batch* b) {
 
 fwi_status fwi_plan_set_schedule(fwi_plan* p, const fwi_schedule* sc) {
   if (!p || !sc) return FWI_EINVAL;
-  if ((sc->specialized != 0 && sc->specialized != 1) || sc->radix_order < 0 || sc->radix_order > 2 ||
+  if (sc->specialized < 0 || sc->specialized > 2 || sc->radix_order < 0 || sc->radix_order > 2 ||
       (sc->z_tile != 16 && sc->z_tile != 32) || (sc->split_plane != 0 && sc->split_plane != 1))
     return FWI_EINVAL;
   const fwi_schedule old = p->sched;

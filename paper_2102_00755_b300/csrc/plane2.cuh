@@ -1,0 +1,486 @@
+// Fused plane kernels with register-resident two-step line transforms for
+// compile-time plane sizes (the momentum and mass halves of one step of Alg. 1,
+// with the k-space derivatives of App. B, Eqs. 18-19, in the xy directions).
+//
+// A CTA owns one z-plane of one simulation.  Per field component the work is
+// seven phases separated by block barriers, over two shared buffers S and X:
+//
+//   1 y-inverse, step A   global spectrum (x or y factor applied) -> DFT_BY1 of the
+//                         stride-BY2 rows of each column, twiddle          -> S
+//   2 y-inverse, step B   DFT_BY2 of each column block                    -> X (rows)
+//   3 x-inverse, step A   C2R packing of rows 2p, 2p+1 into Z = A + iB (Hermitian
+//                         extension), DFT_AX1 of the stride-AX2 subsequences -> S
+//   4 x-inverse, step B   DFT_AX2 gives the derivative at x = k1 + AX1 k2 of both
+//                         rows in registers; PML update of the field (global, read
+//                         and written in place); forward x step A on the new values
+//                         (their subsequence is exactly the stride-AX1 one)   -> X
+//   5 x-forward, step B   DFT_AX1                                          -> S (Z)
+//   6 y-forward, step A   R2C unpacking of rows from Z, DFT_BY1, twiddle   -> X
+//   7 y-forward, step B   DFT_BY2 -> global spectrum
+//
+// Lines are mapped to threads so that every access is conflict-free or
+// coalesced: for the y transforms consecutive threads take consecutive kx; for
+// the x transforms of phase 3 consecutive threads take consecutive row pairs
+// (the pair stride PST is odd); phases 4 and 5 read rows padded to an odd
+// length.  A step-A output of a line of length N = N1 N2 is the sequence
+// Y[j2][k1] = exp(-+2 pi i j2 k1 / N) DFT_N1(x[j2 + N2 j1])[k1], step B gives
+// X[k1 + N1 k2] = DFT_N2(Y[.][k1])[k2].  Twiddle tables are staged in shared
+// memory from the host's FP64-built W_N[k] = exp(-2 pi i k / N).
+#pragma once
+#include "kernels.cuh"
+#include "rfft.cuh"
+
+namespace fwi {
+
+__host__ __device__ constexpr int cmax3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
+
+template <int NX, int NY>
+struct Plane2 {
+  static constexpr int NXc = NX, NYc = NY;
+  static constexpr int HX = NX / 2 + 1;
+  static constexpr int NP = (NY + 1) / 2;
+  static constexpr int AX1 = split_n1(NX), AX2 = NX / AX1;
+  static constexpr int BY1 = split_n1(NY), BY2 = NY / BY1;
+  static constexpr int PA = AX2 + 1;     // padded row of the x-inverse step-A output
+  static constexpr int PB = AX1 + 1;     // padded row of the x-forward step-A output
+  static constexpr int PST = cmax3(2 * HX, AX1 * PA, AX2 * PB) | 1;   // pair stride (odd)
+  // task counts of the phases
+  static constexpr int T1 = HX * BY2, T2 = HX * BY1, T3 = NP * AX2, T4 = NP * AX1;
+  // Threads per CTA (one CTA per SM: the plane buffers take most of shared memory).
+  // Chosen per size so that the phases' task counts fill whole rounds of threads
+  // (e.g. 128: 1040, 520, 1024 and 512 tasks on 544 threads) while the kernels'
+  // registers still fit 64K per SM.
+  static constexpr int NT = NX == 128 ? 544 : NX == 135 ? 352 : NX == 160 ? 416 : NX == 96 ? 416
+                          : NX == 64 ? 288 : 128;
+  static constexpr int TW = NX + NX + NY;                 // twx, twxT, twy
+  static constexpr size_t SMEM = (size_t)(TW + 2 * NP * PST) * 8;
+};
+
+template <class G>
+__device__ __forceinline__ float2* p2_row(float2* buf, int ky) {
+  return buf + (ky >> 1) * G::PST + (ky & 1) * G::HX;
+}
+
+// twiddles: twx[e] = W_NX^e, twxT[k1' AX1 + j2'] = W_NX^(j2' k1'), twy[e] = W_NY^e
+template <class G>
+__device__ __forceinline__ void p2_stage_twiddles(float2* tw, const StepParams& P) {
+  for (int i = threadIdx.x; i < G::TW; i += blockDim.x) {
+    float2 w;
+    if (i < 2 * G::AX1 * G::AX2) {
+      int e = i;
+      if (i >= G::AX1 * G::AX2) {
+        const int t = i - G::AX1 * G::AX2;
+        const int k1p = t / G::AX1, j2p = t - k1p * G::AX1;
+        e = j2p * k1p;
+      }
+      w = P.tw[P.ax.tw_off + e];
+    } else {
+      w = P.tw[P.ay.tw_off + (i - 2 * G::AX1 * G::AX2)];
+    }
+    tw[i] = w;
+  }
+}
+
+// phase 1: global spectrum plane (factor: 0 none, 1 per kx, 2 per ky) -> S
+template <class G>
+__device__ __forceinline__ void p2_yinv_a(float2* S, const float2* __restrict__ src, int fk,
+                                          const float2* __restrict__ fac, const float2* twy) {
+  for (int t = threadIdx.x; t < G::T1; t += G::NT) {
+    const int j2 = t / G::HX, kx = t - j2 * G::HX;
+    float2 a[G::BY1];
+    sfor<0, G::BY1>([&](auto J1) {
+      constexpr int j1 = decltype(J1)::value;
+      a[j1] = __ldg(&src[(j2 + G::BY2 * j1) * G::HX + kx]);
+    });
+    if (fk == 1) {
+      const float2 f = __ldg(&fac[kx]);
+      sfor<0, G::BY1>([&](auto J1) { a[decltype(J1)::value] = cmul(a[decltype(J1)::value], f); });
+    } else if (fk == 2) {
+      sfor<0, G::BY1>([&](auto J1) {
+        constexpr int j1 = decltype(J1)::value;
+        a[j1] = cmul(a[j1], __ldg(&fac[j2 + G::BY2 * j1]));
+      });
+    }
+    RDft<G::BY1, true>::run(a);
+    sfor<1, G::BY1>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      a[k1] = cmulc(a[k1], twy[j2 * k1]);
+    });
+    sfor<0, G::BY1>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      p2_row<G>(S, j2 + G::BY2 * k1)[kx] = a[k1];
+    });
+  }
+}
+
+// phase 2 (INV) and 7 (!INV, to global): column step B
+template <class G, bool INV>
+__device__ __forceinline__ void p2_y_b(const float2* in, float2* out_smem, float2* __restrict__ out_glob) {
+  for (int t = threadIdx.x; t < G::T2; t += G::NT) {
+    const int k1 = t / G::HX, kx = t - k1 * G::HX;
+    float2 a[G::BY2];
+    sfor<0, G::BY2>([&](auto J2) {
+      constexpr int j2 = decltype(J2)::value;
+      a[j2] = p2_row<G>(const_cast<float2*>(in), G::BY2 * k1 + j2)[kx];
+    });
+    RDft<G::BY2, INV>::run(a);
+    if (INV) {
+      sfor<0, G::BY2>([&](auto K2) {
+        constexpr int k2 = decltype(K2)::value;
+        p2_row<G>(out_smem, k1 + G::BY1 * k2)[kx] = a[k2];
+      });
+    } else {
+      sfor<0, G::BY2>([&](auto K2) {
+        constexpr int k2 = decltype(K2)::value;
+        out_glob[(k1 + G::BY1 * k2) * G::HX + kx] = a[k2];
+      });
+    }
+  }
+}
+
+// phase 3: rows (pair-line layout in X) -> C2R packing -> x step A -> S
+template <class G>
+__device__ __forceinline__ void p2_xinv_a(const float2* X, float2* S, const float2* twx) {
+  for (int t = threadIdx.x; t < G::T3; t += G::NT) {
+    const int j2 = t / G::NP, p = t - j2 * G::NP;
+    const float2* ra = X + p * G::PST;
+    const float2* rb = ra + G::HX;
+    const bool hasb = 2 * p + 1 < G::NYc;
+    float2 z[G::AX1];
+    sfor<0, G::AX1>([&](auto J1) {
+      constexpr int j1 = decltype(J1)::value;
+      const int k = j2 + G::AX2 * j1;
+      float2 a, b = make_float2(0.f, 0.f);
+      if (k < G::HX) {
+        a = ra[k];
+        if (hasb) b = rb[k];
+        if (k == 0 || 2 * k == G::NXc) { a.y = 0.f; b.y = 0.f; }
+      } else {
+        const int kk = G::NXc - k;
+        a = ra[kk];
+        if (hasb) b = rb[kk];
+        a.y = -a.y;
+        b.y = -b.y;
+      }
+      z[j1] = make_float2(a.x - b.y, a.y + b.x);
+    });
+    RDft<G::AX1, true>::run(z);
+    sfor<1, G::AX1>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      z[k1] = cmulc(z[k1], twx[j2 * k1]);
+    });
+    float2* o = S + p * G::PST + j2;
+    sfor<0, G::AX1>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      o[k1 * G::PA] = z[k1];
+    });
+  }
+}
+
+// forward x step A of the values z[k2] at x = k1 + AX1 k2 of pair p -> out
+template <class G>
+__device__ __forceinline__ void p2_xfwd_a(float2* z, int p, int k1, float2* out, const float2* twxT) {
+  RDft<G::AX2, false>::run(z);
+  float2* o = out + p * G::PST + k1;
+  sfor<0, G::AX2>([&](auto K1P) {
+    constexpr int k1p = decltype(K1P)::value;
+    const float2 w = k1p == 0 ? make_float2(1.f, 0.f) : twxT[k1p * G::AX1 + k1];
+    o[k1p * G::PB] = k1p == 0 ? z[k1p] : cmul(z[k1p], w);
+  });
+}
+
+// phase 5: x step B (forward) -> Z[k] of each pair in `out`
+template <class G>
+__device__ __forceinline__ void p2_xfwd_b(const float2* in, float2* out) {
+  for (int t = threadIdx.x; t < G::T3; t += G::NT) {
+    const int p = t / G::AX2, k1p = t - p * G::AX2;
+    const float2* r = in + p * G::PST + k1p * G::PB;
+    float2 u[G::AX1];
+    sfor<0, G::AX1>([&](auto J) { u[decltype(J)::value] = r[decltype(J)::value]; });
+    RDft<G::AX1, false>::run(u);
+    float2* o = out + p * G::PST + k1p;
+    sfor<0, G::AX1>([&](auto K2) {
+      constexpr int k2 = decltype(K2)::value;
+      o[G::AX2 * k2] = u[k2];
+    });
+  }
+}
+
+// phase 6: R2C unpacking of rows from Z (in) -> y step A (forward) -> out
+template <class G>
+__device__ __forceinline__ void p2_yfwd_a(const float2* in, float2* out, const float2* twy) {
+  for (int t = threadIdx.x; t < G::T1; t += G::NT) {
+    const int j2 = t / G::HX, kx = t - j2 * G::HX;
+    const int km = kx == 0 ? 0 : G::NXc - kx;
+    float2 a[G::BY1];
+    sfor<0, G::BY1>([&](auto J1) {
+      constexpr int j1 = decltype(J1)::value;
+      const int ky = j2 + G::BY2 * j1;
+      const float2* zp = in + (ky >> 1) * G::PST;
+      const float2 zk = zp[kx], zm = zp[km];
+      a[j1] = (ky & 1) ? make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x))
+                       : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    });
+    RDft<G::BY1, false>::run(a);
+    sfor<1, G::BY1>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      a[k1] = cmul(a[k1], twy[j2 * k1]);
+    });
+    sfor<0, G::BY1>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      p2_row<G>(out, j2 + G::BY2 * k1)[kx] = a[k1];
+    });
+  }
+}
+
+// phase 4, momentum: derivative of both rows in registers, v_comp update in place
+// (Lambda^s (Lambda^s v - dt/rho0 d+ p)), then forward x step A of the new v -> out
+template <class G>
+__device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, const float2* twxT,
+                                              float* __restrict__ v, const float* __restrict__ lam,
+                                              int comp, float lz, float dtr) {
+  for (int t = threadIdx.x; t < G::T4; t += G::NT) {
+    const int p = t / G::AX1, k1 = t - p * G::AX1;
+    const int y0 = 2 * p, y1 = y0 + 1;
+    const bool has1 = y1 < G::NYc;
+    float* v0p = v + y0 * G::NXc + k1;
+    float* v1p = v0p + G::NXc;
+    float s0[G::AX2], s1[G::AX2];
+    sfor<0, G::AX2>([&](auto K2) {
+      constexpr int k2 = decltype(K2)::value;
+      s0[k2] = v0p[G::AX1 * k2];
+      s1[k2] = has1 ? v1p[G::AX1 * k2] : 0.f;
+    });
+    float2 z[G::AX2];
+    const float2* r = S + p * G::PST + k1 * G::PA;
+    sfor<0, G::AX2>([&](auto J) { z[decltype(J)::value] = r[decltype(J)::value]; });
+    RDft<G::AX2, true>::run(z);
+    float l0 = lz, l1 = lz;
+    if (comp == 1) {
+      l0 = __ldg(&lam[y0]);
+      l1 = has1 ? __ldg(&lam[y1]) : 1.f;
+    }
+    sfor<0, G::AX2>([&](auto K2) {
+      constexpr int k2 = decltype(K2)::value;
+      float a0 = l0, a1 = l1;
+      if (comp == 0) a0 = a1 = __ldg(&lam[k1 + G::AX1 * k2]);
+      const float n0 = a0 * (a0 * s0[k2] - dtr * z[k2].x);
+      v0p[G::AX1 * k2] = n0;
+      float n1 = 0.f;
+      if (has1) {
+        n1 = a1 * (a1 * s1[k2] - dtr * z[k2].y);
+        v1p[G::AX1 * k2] = n1;
+      }
+      z[k2] = make_float2(n0, n1);
+    });
+    p2_xfwd_a<G>(z, p, k1, out, twxT);
+  }
+}
+
+// phase 4, mass: rho_comp <- Lambda (Lambda rho - dt rho0 d- v); for the last
+// component also p = c0^2 (rho_x + rho_y + rho_z), written as pairs to pout.
+template <class G, bool LAST>
+__device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, float* __restrict__ rho,
+                                               const float* __restrict__ lam, int comp, float lz,
+                                               float dtr0, const float* rx, const float* rz,
+                                               const float* __restrict__ c2) {
+  for (int t = threadIdx.x; t < G::T4; t += G::NT) {
+    const int p = t / G::AX1, k1 = t - p * G::AX1;
+    const int y0 = 2 * p, y1 = y0 + 1;
+    const bool has1 = y1 < G::NYc;
+    const int o0 = y0 * G::NXc + k1, o1 = o0 + G::NXc;
+    float s0[G::AX2], s1[G::AX2];
+    sfor<0, G::AX2>([&](auto K2) {
+      constexpr int k2 = decltype(K2)::value;
+      s0[k2] = rho[o0 + G::AX1 * k2];
+      s1[k2] = has1 ? rho[o1 + G::AX1 * k2] : 0.f;
+    });
+    float2 z[G::AX2];
+    const float2* r = S + p * G::PST + k1 * G::PA;
+    sfor<0, G::AX2>([&](auto J) { z[decltype(J)::value] = r[decltype(J)::value]; });
+    RDft<G::AX2, true>::run(z);
+    float l0 = lz, l1 = lz;
+    if (comp == 1) {
+      l0 = __ldg(&lam[y0]);
+      l1 = has1 ? __ldg(&lam[y1]) : 1.f;
+    }
+    float2* po = pout + p * G::PST + k1;
+    sfor<0, G::AX2>([&](auto K2) {
+      constexpr int k2 = decltype(K2)::value;
+      constexpr int xo = G::AX1 * k2;
+      float a0 = l0, a1 = l1;
+      if (comp == 0) a0 = a1 = __ldg(&lam[k1 + xo]);
+      const float r0 = a0 * (a0 * s0[k2] - dtr0 * z[k2].x);
+      rho[o0 + xo] = r0;
+      float r1 = 0.f;
+      if (has1) {
+        r1 = a1 * (a1 * s1[k2] - dtr0 * z[k2].y);
+        rho[o1 + xo] = r1;
+      }
+      if (LAST) {
+        const float p0v = __ldg(&c2[o0 + xo]) * (rx[o0 + xo] + r0 + rz[o0 + xo]);
+        const float p1v = has1 ? __ldg(&c2[o1 + xo]) * (rx[o1 + xo] + r1 + rz[o1 + xo]) : 0.f;
+        po[xo] = make_float2(p0v, p1v);
+      }
+    });
+  }
+}
+
+// float offset pf of the pair-line plane buffer (regions of 2 hx complex) -> the
+// same voxel in a buffer of pair stride PST
+template <class G>
+__device__ __forceinline__ int p2_pf(int pf) {
+  const int q = pf / (4 * G::HX);
+  return pf + q * (2 * G::PST - 4 * G::HX);
+}
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mom(const __grid_constant__ StepParams P) {
+  using G = Plane2<NX, NY>;
+  if (*P.bad) return;
+  extern __shared__ float2 sm2[];
+  const float2* twx = sm2;
+  const float2* twxT = sm2 + NX;
+  const float2* twy = sm2 + 2 * NX;
+  float2* S = sm2 + G::TW;
+  float2* X = S + G::NP * G::PST;
+  p2_stage_twiddles<G>(sm2, P);
+  __syncthreads();
+  const int z = blockIdx.x;
+  const SimPtrs& Q = P.sims[blockIdx.y];
+  const size_t soff = (size_t)z * (G::HX * NY);
+  const size_t voff = (size_t)z * (NX * NY);
+  // component order z, x, y: R -> V_z (spec[1]), Q -> V_x (spec[2]), Q -> V_y (spec[0])
+#pragma unroll 1
+  for (int cc = 0; cc < 3; ++cc) {
+    const int comp = cc == 0 ? 2 : cc - 1;
+    const float2* src = (comp == 2 ? Q.spec[1] : Q.spec[0]) + soff;
+    float2* dst = (comp == 2 ? Q.spec[1] : (comp == 0 ? Q.spec[2] : Q.spec[0])) + soff;
+    const float lz = __ldg(&P.lams[2][z]);
+    p2_yinv_a<G>(S, src, comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.ap[comp], twy);
+    __syncthreads();
+    p2_y_b<G, true>(S, X, nullptr);
+    __syncthreads();
+    p2_xinv_a<G>(X, S, twx);
+    __syncthreads();
+    p2_mom_update<G>(S, X, twxT, Q.v[comp] + voff, P.lams[comp], comp, lz, P.dt_over_rho0);
+    __syncthreads();
+    p2_xfwd_b<G>(X, S);
+    __syncthreads();
+    p2_yfwd_a<G>(S, X, twy);
+    __syncthreads();
+    p2_y_b<G, false>(X, nullptr, dst);
+    // the next component writes S (last read before the previous barrier) and reads
+    // a global plane this component does not write
+  }
+}
+
+template <int NX, int NY>
+__global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __grid_constant__ StepParams P) {
+  using G = Plane2<NX, NY>;
+  if (*P.bad) return;
+  extern __shared__ float2 sm2[];
+  const float2* twx = sm2;
+  const float2* twxT = sm2 + NX;
+  const float2* twy = sm2 + 2 * NX;
+  float2* S = sm2 + G::TW;
+  float2* X = S + G::NP * G::PST;
+  p2_stage_twiddles<G>(sm2, P);
+  __syncthreads();
+  const int z = blockIdx.x;
+  const SimPtrs& Q = P.sims[blockIdx.y];
+  const int role = Q.role, shot = Q.shot, tix = P.tidx[blockIdx.y];
+  const size_t soff = (size_t)z * (G::HX * NY);
+  const size_t voff = (size_t)z * (NX * NY);
+  const float lz = __ldg(&P.lam[2][z]);
+  // component order x (spec[2]), z (spec[1]), y (spec[0]); the last one assembles p
+#pragma unroll 1
+  for (int cc = 0; cc < 2; ++cc) {
+    const int comp = cc == 0 ? 0 : 2;
+    const float2* src = (comp == 0 ? Q.spec[2] : Q.spec[1]) + soff;
+    p2_yinv_a<G>(S, src, comp == 0 ? 1 : 0, P.am[comp], twy);
+    __syncthreads();
+    p2_y_b<G, true>(S, X, nullptr);
+    __syncthreads();
+    p2_xinv_a<G>(X, S, twx);
+    __syncthreads();
+    p2_mass_update<G, false>(S, nullptr, Q.rho[comp] + voff, P.lam[comp], comp, lz, P.dt_rho0, nullptr,
+                             nullptr, nullptr);
+    __syncthreads();
+  }
+  p2_yinv_a<G>(S, Q.spec[0] + soff, 2, P.am[1], twy);
+  __syncthreads();
+  p2_y_b<G, true>(S, X, nullptr);
+  __syncthreads();
+  p2_xinv_a<G>(X, S, twx);
+  __syncthreads();
+  p2_mass_update<G, true>(S, X, Q.rho[1] + voff, P.lam[1], 1, lz, P.dt_rho0, Q.rho[0] + voff,
+                          Q.rho[2] + voff, P.c2 + voff);
+  __syncthreads();
+  // sparse updates of rho_xi and p on this plane, then recording
+  const int key0 = z * G::NP, key1 = key0 + G::NP;
+  float* zf = reinterpret_cast<float*>(X);
+  if (role == ROLE_FORWARD) {
+    const float* amp = P.amp_src + ((size_t)shot * P.nt + tix) * P.n_us;
+    for (int u = P.us_ptr[key0] + threadIdx.x; u < P.us_ptr[key1]; u += G::NT) {
+      const int vx = P.us_vox[u];
+      const float a = amp[u];
+      Q.rho[0][vx] += a;
+      Q.rho[1][vx] += a;
+      Q.rho[2][vx] += a;
+      zf[p2_pf<G>(P.us_pf[u])] += P.c2[vx] * (3.f * a);
+    }
+  } else if (role == ROLE_ADJOINT) {
+    const float* q = P.qf + ((size_t)shot * P.nt + tix) * P.n_rec;
+    for (int u = P.ur_ptr[key0] + threadIdx.x; u < P.ur_ptr[key1]; u += G::NT) {
+      float s = 0.f;
+      for (int e = P.ur_mptr[u]; e < P.ur_mptr[u + 1]; ++e) s += q[P.ur_mem[e]];
+      const float a = P.ur_coef[u] * s;
+      const int vx = P.ur_vox[u];
+      Q.rho[0][vx] += a;
+      Q.rho[1][vx] += a;
+      Q.rho[2][vx] += a;
+      zf[p2_pf<G>(P.ur_pf[u])] += P.c2[vx] * (3.f * a);
+    }
+  } else {  // TR: rho_xi(layer) <- g^(Nt - m) / (3 c0^2)
+    const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1 - tix)) * P.n_layer;
+    for (int j = P.lay_ptr[key0] + threadIdx.x; j < P.lay_ptr[key1]; j += G::NT) {
+      const int vx = P.lay_vox[j];
+      const float val = g[j] * P.inv3c2[j];
+      Q.rho[0][vx] = val;
+      Q.rho[1][vx] = val;
+      Q.rho[2][vx] = val;
+      zf[p2_pf<G>(P.lay_pf[j])] = P.c2[vx] * (3.f * val);
+    }
+  }
+  __syncthreads();
+  if (role == ROLE_FORWARD) {
+    float* f = P.traces + ((size_t)shot * P.nt + tix) * P.n_rec;
+    for (int e = P.rr_ptr[key0] + threadIdx.x; e < P.rr_ptr[key1]; e += G::NT) f[P.rr_col[e]] = zf[p2_pf<G>(P.rr_pf[e])];
+    if (P.record_layer) {
+      float* g = P.ghist + ((size_t)shot * P.nt + tix) * P.n_layer;
+      for (int j = P.lay_ptr[key0] + threadIdx.x; j < P.lay_ptr[key1]; j += G::NT) g[j] = zf[p2_pf<G>(P.lay_pf[j])];
+    }
+  } else {
+    float* out = role == ROLE_ADJOINT ? P.pa + (size_t)shot * P.n_gamma
+                                      : P.ring + ((size_t)shot * 3 + P.slot[blockIdx.y]) * P.n_gamma;
+    for (int j = P.gam_ptr[key0] + threadIdx.x; j < P.gam_ptr[key1]; j += G::NT) out[j] = zf[p2_pf<G>(P.gam_pf[j])];
+  }
+  __syncthreads();
+  // forward x step A of p (pairs in X) -> S, then step B, R2C unpacking and y
+  for (int t = threadIdx.x; t < G::T4; t += G::NT) {
+    const int p = t / G::AX1, k1 = t - p * G::AX1;
+    const float2* r = X + p * G::PST + k1;
+    float2 zz[G::AX2];
+    sfor<0, G::AX2>([&](auto K2) { zz[decltype(K2)::value] = r[G::AX1 * decltype(K2)::value]; });
+    p2_xfwd_a<G>(zz, p, k1, S, twxT);
+  }
+  __syncthreads();
+  p2_xfwd_b<G>(S, X);
+  __syncthreads();
+  p2_yfwd_a<G>(X, S, twy);
+  __syncthreads();
+  p2_y_b<G, false>(S, nullptr, Q.spec[0] + soff);
+}
+
+}  // namespace fwi

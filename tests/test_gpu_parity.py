@@ -196,3 +196,29 @@ def test_split_plane_path_gradient_parity(pairing):
         assert oc.rel(traces[k].cpu().numpy(), f_ref[k]) < TOL_TRACES
     assert np.all(np.abs(D.cpu().numpy() - D_ref) <= TOL_MISFIT * np.abs(D_ref))
     assert oc.rel(g.cpu().numpy().reshape(wl.shape), g_ref) < TOL_GRAD
+
+
+@pytest.mark.parametrize("shape,pairing", [((32, 32, 20), "literal"), ((64, 64, 12), "exact"),
+                                           ((96, 96, 10), "literal"), ((135, 135, 8), "exact"),
+                                           ((160, 160, 8), "literal")])
+def test_two_step_plane_kernels_gradient_parity(shape, pairing):
+    """The two-step register-transform plane kernels (schedule specialized = 2) on every
+    plane size they are built for: forward traces, misfit and gradient (adjoint and
+    time-reversal roles of the mass kernel) against the oracle."""
+    from paper_2102_00755_b300 import autotune
+    # 0.5 MHz over 90 steps: the pulse crosses Gamma, so the residual is a few percent of
+    # the traces (a misfit of rounding-level residuals would only measure FP32 noise)
+    wl = synth.small_workload(*shape, 90, pml=3, n_src=3, n_rec=20, K=2, layer=2, seed=11,
+                              f0=0.5e6, gamma_frac=0.3)
+    f_obs = oc.observed(wl)
+    f_ref, D_ref, g_ref = oc.gradient(wl, f_obs, pairing, c_rec=wl.c_rec)
+    plan = fwi.Plan.from_workload(wl, pairing=pairing, max_shots=len(wl.weights))
+    sched = dict(specialized=2, radix_order=0, z_tile=32, split_plane=0)
+    assert autotune.set_schedule(plan, sched) == fwi.FWI_OK
+    traces = torch.empty((len(wl.weights), wl.nt, len(wl.rec_idx)), dtype=torch.float32, device="cuda")
+    D, g = plan.gradient(dev(wl.c_model), dev(wl.weights), dev(f_obs), traces=traces)
+    assert plan.status() == fwi.FWI_OK
+    for k in range(len(wl.weights)):
+        assert oc.rel(traces[k].cpu().numpy(), f_ref[k]) < TOL_TRACES
+    assert np.all(np.abs(D.cpu().numpy() - D_ref) <= TOL_MISFIT * np.abs(D_ref))
+    assert oc.rel(g.cpu().numpy().reshape(wl.shape), g_ref) < TOL_GRAD
