@@ -19,7 +19,7 @@ from . import fwi
 
 CANDIDATES = [dict(specialized=s, radix_order=r, z_tile=t, split_plane=sp)
               for sp in (0, 1) for s in (2, 1, 0) for r in (0, 1, 2) for t in (32, 16)
-              if not (s >= 1 and r != 0) and not (sp == 1 and s >= 1)]
+              if not (s >= 1 and r != 0) and not (sp == 1 and s == 1)]
 KNOBS = ("specialized", "radix_order", "z_tile", "split_plane")
 
 

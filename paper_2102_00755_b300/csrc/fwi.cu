@@ -267,6 +267,8 @@ struct fwi_plan {
   int fxy;   // specialised plane side (0: runtime schedules)
   int p2;    // plane side of the two-step register-transform plane kernels (0: not used)
   size_t smem_p2;
+  int z2;    // nz of the two-step register-transform z pass (0: not used)
+  size_t smem_z2[2];
   int fz;    // specialised z length (0: runtime schedules)
   int tz;    // z-pass tile width (columns)
   int split; // XY work split into column and row-pair passes (large planes)
@@ -407,6 +409,21 @@ fwi_status cuda_fail(cudaError_t e, const char* what) {
     case 160: { constexpr int N = 160; CALL; } break;                   \
     default: break;                                                     \
   }
+#define Z2_DISPATCH_T(p, TZ, CALL)                                      \
+  switch ((p)->z2) {                                                    \
+    case 32: { constexpr int NZ = 32; CALL; } break;                    \
+    case 48: { constexpr int NZ = 48; CALL; } break;                    \
+    case 64: { constexpr int NZ = 64; CALL; } break;                    \
+    case 80: { constexpr int NZ = 80; CALL; } break;                    \
+    case 96: { constexpr int NZ = 96; CALL; } break;                    \
+    case 128: { constexpr int NZ = 128; CALL; } break;                  \
+    case 135: { constexpr int NZ = 135; CALL; } break;                  \
+    case 256: { constexpr int NZ = 256; CALL; } break;                  \
+    default: break;                                                     \
+  }
+#define Z2_DISPATCH(p, CALL)                                            \
+  if ((p)->tz == 32) { constexpr int TZ = 32; Z2_DISPATCH_T(p, TZ, CALL) } \
+  else { constexpr int TZ = 16; Z2_DISPATCH_T(p, TZ, CALL) }
 #define Z_DISPATCH_T(p, TZ, CALL)                                       \
   switch ((p)->fz) {                                                    \
     case 32: { constexpr int E = 8, FZ = 32; CALL; } break;             \
@@ -445,6 +462,11 @@ void set_attrs_p2(int cap) {
   cudaFuncSetAttribute(k_plane2_mom<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_plane2_mass<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
+template <int NZ, int TZ>
+void set_attrs_z2(int cap) {
+  cudaFuncSetAttribute(k_zpass2<0, NZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_zpass2<1, NZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
 template <int E, int FZ, int TZ>
 void set_attrs_z(int cap) {
   cudaFuncSetAttribute(k_zpass<0, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
@@ -467,6 +489,7 @@ void set_attrs(fwi_plan* p) {
   else set_attrs_split<16>(cap);
   PLANE_DISPATCH(p, (set_attrs_plane<E, F>(cap)));
   P2_DISPATCH(p, (set_attrs_p2<N>(cap)));
+  Z2_DISPATCH(p, (set_attrs_z2<NZ, TZ>(cap)));
   Z_DISPATCH(p, (set_attrs_z<E, FZ, TZ>(cap)));
   // Touch every small kernel too, so that modules are loaded before any stream
   // capture of a call (a first launch inside a capture may not load them).
@@ -505,8 +528,13 @@ fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   const dim3 gx2((p->npair + warps * g2 - 1) / (warps * g2), p->prob.nz, P.nsims);
   int slot;
   prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
-  Z_DISPATCH(p, (k_zpass<0, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
-  LAUNCHED("k_zpass<momentum>");
+  if (p->z2) {
+    Z2_DISPATCH(p, (k_zpass2<0, NZ, TZ><<<gz, Z2<NZ, TZ>::NT, p->smem_z2[0], st>>>(P)));
+    LAUNCHED("k_zpass2<momentum>");
+  } else {
+    Z_DISPATCH(p, (k_zpass<0, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+    LAUNCHED("k_zpass<momentum>");
+  }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
   k_ypass<Y_INV_MOM, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
@@ -517,8 +545,13 @@ fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   LAUNCHED("k_ypass<forward x3>");
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
-  Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
-  LAUNCHED("k_zpass<mass>");
+  if (p->z2) {
+    Z2_DISPATCH(p, (k_zpass2<1, NZ, TZ><<<gz, Z2<NZ, TZ>::NT, p->smem_z2[1], st>>>(P)));
+    LAUNCHED("k_zpass2<mass>");
+  } else {
+    Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+    LAUNCHED("k_zpass<mass>");
+  }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
   k_ypass<Y_INV_MASS, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
@@ -537,8 +570,13 @@ fwi_status launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   const dim3 gp(p->prob.nz, P.nsims);
   int slot;
   prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
-  Z_DISPATCH(p, (k_zpass<0, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
-  LAUNCHED("k_zpass<momentum>");
+  if (p->z2) {
+    Z2_DISPATCH(p, (k_zpass2<0, NZ, TZ><<<gz, Z2<NZ, TZ>::NT, p->smem_z2[0], st>>>(P)));
+    LAUNCHED("k_zpass2<momentum>");
+  } else {
+    Z_DISPATCH(p, (k_zpass<0, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+    LAUNCHED("k_zpass<momentum>");
+  }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
   if (p->p2) {
@@ -550,8 +588,13 @@ fwi_status launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
-  Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
-  LAUNCHED("k_zpass<mass>");
+  if (p->z2) {
+    Z2_DISPATCH(p, (k_zpass2<1, NZ, TZ><<<gz, Z2<NZ, TZ>::NT, p->smem_z2[1], st>>>(P)));
+    LAUNCHED("k_zpass2<mass>");
+  } else {
+    Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+    LAUNCHED("k_zpass<mass>");
+  }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
   if (p->p2) {
@@ -597,15 +640,24 @@ fwi_status apply_schedule(fwi_plan* p) {
   p->split = sc.split_plane;
   p->fxy = (!p->split && sc.specialized && q.nx == q.ny && in(q.nx, {32, 64, 96, 128, 160})) ? q.nx : 0;
   p->fz = (sc.specialized && in(q.nz, {32, 48, 64, 80, 96, 128})) ? q.nz : 0;
+  p->tz = sc.z_tile;
   p->p2 = 0;
   p->smem_p2 = 0;
-  if (sc.specialized == 2) {
-    if (p->split || q.nx != q.ny || !in(q.nx, {32, 64, 96, 128, 135, 160})) return FWI_ENOTSUP;
-    p->p2 = q.nx;
-    P2_DISPATCH(p, (p->smem_p2 = Plane2<N, N>::SMEM));
-    if (p->smem_p2 > 227 * 1024) return FWI_ENOTSUP;
+  p->z2 = 0;
+  p->smem_z2[0] = p->smem_z2[1] = 0;
+  if (sc.specialized == 2) {   // two-step kernels where built (planes, z pass or both)
+    if (!p->split && q.nx == q.ny && in(q.nx, {32, 64, 96, 128, 135, 160})) {
+      p->p2 = q.nx;
+      P2_DISPATCH(p, (p->smem_p2 = Plane2<N, N>::SMEM));
+      if (p->smem_p2 > 227 * 1024) p->p2 = 0;
+    }
+    if (in(q.nz, {32, 48, 64, 80, 96, 128, 135, 256})) {
+      p->z2 = q.nz;
+      Z2_DISPATCH(p, (p->smem_z2[0] = Z2<NZ, TZ>::smem(0), p->smem_z2[1] = Z2<NZ, TZ>::smem(1)));
+      if (p->smem_z2[0] > 227 * 1024) p->z2 = 0;
+    }
+    if (!p->p2 && !p->z2) return FWI_ENOTSUP;
   }
-  p->tz = sc.z_tile;
   const int tw_x = p->ax.tw_off, tw_y = p->ay.tw_off, tw_z = p->az.tw_off;
   if (!factor235(q.nx, &p->ax, sc.radix_order) || !factor235(q.ny, &p->ay, sc.radix_order) ||
       !factor235(q.nz, &p->az, sc.radix_order))

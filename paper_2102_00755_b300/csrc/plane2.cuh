@@ -484,3 +484,132 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
 }
 
 }  // namespace fwi
+
+namespace fwi {
+
+// ---------------------------------------------------------------------------
+// z pass with two-step register transforms (compile-time nz).  A CTA holds TZ
+// adjacent (ky, kx) spectrum columns; consecutive threads take consecutive
+// columns, so global rows are read and written as TZ * 8 contiguous bytes and
+// shared rows [z][TZ] are conflict-free.  Per column and output:
+//   forward step A (from global) -> smem -> forward step B gives X[kz] at
+//   kz = k1 + N1 k2 in registers -> times kappa / N (and the z factor) ->
+//   inverse step A on that stride-N1 subsequence -> smem -> inverse step B
+//   -> global.
+// MODE 0 (momentum): spec[0] -> Q (spec[0]) and R = Q a+_z (spec[1]).
+// MODE 1 (mass): spec[2] (x), spec[0] (y), spec[1] (z, times a-_z), in place.
+template <int NZ, int TZ>
+struct Z2 {
+  static constexpr int N1 = split_n1(NZ), N2 = NZ / N1;
+  static constexpr int NT = TZ * N2;                 // forward step A: one task per thread
+  static constexpr int TW = NZ + NZ;                 // W_NZ^e and the transposed table
+  static constexpr size_t smem(int mode) { return (size_t)(TW + (mode == 0 ? 3 : 2) * NZ * TZ) * 8; }
+};
+
+template <int MODE, int NZ, int TZ>
+__global__ void __launch_bounds__(Z2<NZ, TZ>::NT) k_zpass2(const __grid_constant__ StepParams P) {
+  using C = Z2<NZ, TZ>;
+  constexpr int N1 = C::N1, N2 = C::N2;
+  if (*P.bad) return;
+  extern __shared__ float2 zs2[];
+  float2* tw = zs2;                     // tw[e] = W^e, e < NZ
+  float2* twT = zs2 + NZ;               // twT[k1' N1 + k1] = W^(k1 k1'), k1' < N2, k1 < N1
+  float2* b0 = zs2 + C::TW;
+  float2* b1 = b0 + NZ * TZ;
+  float2* b2 = b1 + NZ * TZ;
+  for (int i = threadIdx.x; i < C::TW; i += C::NT) {
+    int e = i;
+    if (i >= NZ) {
+      const int t = i - NZ, k1p = t / N1, k1 = t - k1p * N1;
+      e = k1 * k1p;
+    }
+    tw[i] = P.tw[P.az.tw_off + e];
+  }
+  const SimPtrs& Q = P.sims[blockIdx.y];
+  const int M = P.mspec;
+  const int m0 = blockIdx.x * TZ;
+  const float rhx = 1.0f / (float)P.hx;
+  const int nslot = MODE == 0 ? 1 : 3;
+#pragma unroll 1
+  for (int s = 0; s < nslot; ++s) {
+    const float2* src = MODE == 0 ? Q.spec[0] : (s == 0 ? Q.spec[2] : (s == 1 ? Q.spec[0] : Q.spec[1]));
+    __syncthreads();   // twiddles staged; previous slot's buffers consumed
+    // forward step A: DFT_N1 of x[j2 + N2 j1] from global, twiddle -> b0
+    {
+      const int ml = threadIdx.x % TZ, j2 = threadIdx.x / TZ;
+      const int m = m0 + ml;
+      float2 a[N1];
+      sfor<0, N1>([&](auto J1) {
+        constexpr int j1 = decltype(J1)::value;
+        a[j1] = m < M ? __ldg(&src[(size_t)(j2 + N2 * j1) * M + m]) : make_float2(0.f, 0.f);
+      });
+      RDft<N1, false>::run(a);
+      sfor<0, N1>([&](auto K1) {
+        constexpr int k1 = decltype(K1)::value;
+        b0[(j2 + N2 * k1) * TZ + ml] = k1 == 0 ? a[k1] : cmul(a[k1], tw[j2 * k1]);
+      });
+    }
+    __syncthreads();
+    // forward step B, kappa, inverse step A (per output) -> b1 (, b2)
+    for (int t = threadIdx.x; t < TZ * N1; t += C::NT) {
+      const int ml = t % TZ, k1 = t / TZ;
+      const int m = m0 + ml;
+      float2 x[N2];
+      sfor<0, N2>([&](auto J2) { x[decltype(J2)::value] = b0[(N2 * k1 + decltype(J2)::value) * TZ + ml]; });
+      RDft<N2, false>::run(x);
+      const int mm = m < M ? m : M - 1;
+      const int ky = fdivi(mm, rhx);
+      const int kx = mm - ky * P.hx;
+      const float kxy = __ldg(&P.kx2[kx]) + __ldg(&P.ky2[ky]);
+      float2 r[N2];
+      sfor<0, N2>([&](auto K2) {
+        constexpr int k2 = decltype(K2)::value;
+        const int kz = k1 + N1 * k2;
+        const float a = P.half_cdt * sqrtf(kxy + __ldg(&P.kz2[kz]));
+        const float kap = (a > 0.f ? sinf(a) / a : 1.f) * P.inv_n;
+        const float2 v = cscale(x[k2], kap);
+        if constexpr (MODE == 0) {
+          x[k2] = v;
+          r[k2] = cmul(v, __ldg(&P.ap[2][kz]));
+        } else {
+          x[k2] = (s == 2) ? cmul(v, __ldg(&P.am[2][kz])) : v;
+        }
+      });
+      // inverse: the held values are the stride-N1 subsequence kz = k1 + N1 k2
+      RDft<N2, true>::run(x);
+      sfor<0, N2>([&](auto K1P) {
+        constexpr int k1p = decltype(K1P)::value;
+        b1[(k1p * N1 + k1) * TZ + ml] = k1p == 0 ? x[k1p] : cmulc(x[k1p], twT[k1p * N1 + k1]);
+      });
+      if constexpr (MODE == 0) {
+        RDft<N2, true>::run(r);
+        sfor<0, N2>([&](auto K1P) {
+          constexpr int k1p = decltype(K1P)::value;
+          b2[(k1p * N1 + k1) * TZ + ml] = k1p == 0 ? r[k1p] : cmulc(r[k1p], twT[k1p * N1 + k1]);
+        });
+      }
+    }
+    __syncthreads();
+    // inverse step B: DFT_N1 over k1 for each k1', output z = k1' + N2 k2' -> global
+    for (int t = threadIdx.x; t < TZ * N2; t += C::NT) {
+      const int ml = t % TZ, k1p = t / TZ;
+      const int m = m0 + ml;
+      for (int o = 0; o < (MODE == 0 ? 2 : 1); ++o) {
+        const float2* bb = o == 0 ? b1 : b2;
+        float2* dst = MODE == 0 ? (o == 0 ? Q.spec[0] : Q.spec[1])
+                                : (s == 0 ? Q.spec[2] : (s == 1 ? Q.spec[0] : Q.spec[1]));
+        float2 u[N1];
+        sfor<0, N1>([&](auto K1) { u[decltype(K1)::value] = bb[(k1p * N1 + decltype(K1)::value) * TZ + ml]; });
+        RDft<N1, true>::run(u);
+        if (m < M) {
+          sfor<0, N1>([&](auto K2P) {
+            constexpr int k2p = decltype(K2P)::value;
+            dst[(size_t)(k1p + N2 * k2p) * M + m] = u[k2p];
+          });
+        }
+      }
+    }
+  }
+}
+
+}  // namespace fwi

@@ -199,7 +199,8 @@ def test_split_plane_path_gradient_parity(pairing):
 
 
 @pytest.mark.parametrize("shape,pairing", [((32, 32, 20), "literal"), ((64, 64, 12), "exact"),
-                                           ((96, 96, 10), "literal"), ((135, 135, 8), "exact"),
+                                           ((96, 96, 10), "literal"), ((128, 128, 8), "exact"),
+                                           ((135, 135, 8), "exact"),
                                            ((160, 160, 8), "literal")])
 def test_two_step_plane_kernels_gradient_parity(shape, pairing):
     """The two-step register-transform plane kernels (schedule specialized = 2) on every
