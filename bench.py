@@ -307,6 +307,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--nt", type=int, default=0,
                     help="override the number of time samples (small profiling cases only)")
+    ap.add_argument("--schedule", default="",
+                    help="fixed FFT schedule 'specialized,radix_order,z_tile,split_plane' instead of "
+                         "autotuning (reproducible launch sequences for profiling)")
     ap.add_argument("--requests", type=int, default=64, help="serve: length of the request stream")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--inflight", type=int, default=8, help="serve: admitted requests at most")
@@ -348,9 +351,13 @@ def main():
         rng = np.random.default_rng(1000 + rank)
         wl.weights = np.stack([synth.rademacher(len(wl.src_idx), rng) for _ in range(K)])
     from paper_2102_00755_b300 import autotune
-    schedule = autotune.tune(wl, K=K, steps=24, reps=3, device=dev, save=False)["schedule"]
+    if args.schedule:
+        schedule = dict(zip(autotune.KNOBS, (int(v) for v in args.schedule.split(","))))
+    else:
+        schedule = autotune.tune(wl, K=K, steps=24, reps=3, device=dev, save=False)["schedule"]
     plan = fwi.Plan.from_workload(wl, pairing="literal", max_shots=K, device=dev)
-    autotune.set_schedule(plan, schedule)
+    if autotune.set_schedule(plan, schedule) != fwi.FWI_OK:
+        raise RuntimeError(f"schedule {schedule} is not available for this grid")
     c_true = torch.tensor(wl.c_true, dtype=torch.float32, device=dev).reshape(-1)
     c_model = torch.tensor(wl.c_model, dtype=torch.float32, device=dev).reshape(-1)
     w = torch.tensor(wl.weights, dtype=torch.float32, device=dev)
@@ -365,13 +372,15 @@ def main():
     def step():
         plan.gradient(c_model, w, observed, misfit=misfit, grad=grad)
 
-    # warm-up; the first warm-up step times every kernel (CUDA events) for the time shares
+    # warm-up; the last warm-up step times every kernel (CUDA events) for the time shares
+    # (the first calls also load modules and would distort them)
     share_ms = {}
     for i in range(args.warmup):
-        if i == 0:
+        last = i == args.warmup - 1
+        if last:
             plan.profile(enable=True)
         step()
-        if i == 0:
+        if last:
             plan.profile(enable=False)
             share_ms = {k: v[0] for k, v in plan.profile_read().items()}
         flush.zero_()

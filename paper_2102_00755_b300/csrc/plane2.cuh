@@ -53,8 +53,43 @@ struct Plane2 {
   static constexpr int NT = NX == 128 ? 544 : NX == 135 ? 352 : NX == 160 ? 416 : NX == 96 ? 416
                           : NX == 64 ? 288 : 128;
   static constexpr int TW = NX + NX + NY;                 // twx, twxT, twy
-  static constexpr size_t SMEM = (size_t)(TW + 2 * NP * PST) * 8;
+  // staging buffer (complex units) for the next global input: a spectrum plane, or a
+  // real field plane with rows padded to NX + 4 floats (conflict-free phase-4 reads)
+  static constexpr int RS = NX + 4;
+  static constexpr int GS = (HX * NY > (NY * RS + 1) / 2) ? HX * NY : (NY * RS + 1) / 2;
+  static constexpr int TWP = (TW + 1) & ~1;              // keeps the buffers 16-byte aligned
+  static constexpr size_t SMEM_NOSTAGE = (size_t)(TWP + 2 * NP * PST) * 8;
+  static constexpr bool STAGE = SMEM_NOSTAGE + (size_t)GS * 8 <= 227 * 1024 && (HX * NY) % 2 == 0;
+  static constexpr size_t SMEM = SMEM_NOSTAGE + (STAGE ? (size_t)GS * 8 : 0);
 };
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// asynchronous copy of a spectrum plane (HX * NY complex, contiguous) into G
+template <class G>
+__device__ __forceinline__ void p2_fetch_spec(float2* Gb, const float2* __restrict__ src) {
+  static_assert((G::HX * G::NYc) % 2 == 0, "spectrum planes are copied in 16-byte pieces");
+  static_assert((G::TWP + G::NP * G::PST) % 2 == 0, "buffers must start on 16-byte boundaries");
+  constexpr int n16 = G::HX * G::NYc / 2;
+  for (int i = threadIdx.x; i < n16; i += G::NT) cp_async16(Gb + 2 * i, src + 2 * i);
+  cp_async_commit();
+}
+// asynchronous copy of a real field plane (NY rows of NX floats) into G, rows padded
+template <class G>
+__device__ __forceinline__ void p2_fetch_rows(float2* Gb, const float* __restrict__ src) {
+  static_assert(G::NXc % 4 == 0, "rows are copied in 16-byte pieces");
+  constexpr int per_row = G::NXc / 4;
+  float* d = reinterpret_cast<float*>(Gb);
+  for (int i = threadIdx.x; i < G::NYc * per_row; i += G::NT) {
+    const int y = i / per_row, c = i - y * per_row;
+    cp_async16(d + y * G::RS + 4 * c, src + y * G::NXc + 4 * c);
+  }
+  cp_async_commit();
+}
 
 template <class G>
 __device__ __forceinline__ float2* p2_row(float2* buf, int ky) {
@@ -83,14 +118,14 @@ __device__ __forceinline__ void p2_stage_twiddles(float2* tw, const StepParams& 
 
 // phase 1: global spectrum plane (factor: 0 none, 1 per kx, 2 per ky) -> S
 template <class G>
-__device__ __forceinline__ void p2_yinv_a(float2* S, const float2* __restrict__ src, int fk,
+__device__ __forceinline__ void p2_yinv_a(float2* S, const float2* src, int fk,
                                           const float2* __restrict__ fac, const float2* twy) {
   for (int t = threadIdx.x; t < G::T1; t += G::NT) {
     const int j2 = t / G::HX, kx = t - j2 * G::HX;
     float2 a[G::BY1];
     sfor<0, G::BY1>([&](auto J1) {
       constexpr int j1 = decltype(J1)::value;
-      a[j1] = __ldg(&src[(j2 + G::BY2 * j1) * G::HX + kx]);
+      a[j1] = src[(j2 + G::BY2 * j1) * G::HX + kx];   // staged plane (shared) or global
     });
     if (fk == 1) {
       const float2 f = __ldg(&fac[kx]);
@@ -237,19 +272,21 @@ __device__ __forceinline__ void p2_yfwd_a(const float2* in, float2* out, const f
 // (Lambda^s (Lambda^s v - dt/rho0 d+ p)), then forward x step A of the new v -> out
 template <class G>
 __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, const float2* twxT,
-                                              float* __restrict__ v, const float* __restrict__ lam,
-                                              int comp, float lz, float dtr) {
+                                              float* __restrict__ v, const float* vin, int rs,
+                                              const float* __restrict__ lam, int comp, float lz, float dtr) {
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
     const int p = t / G::AX1, k1 = t - p * G::AX1;
     const int y0 = 2 * p, y1 = y0 + 1;
     const bool has1 = y1 < G::NYc;
     float* v0p = v + y0 * G::NXc + k1;
     float* v1p = v0p + G::NXc;
+    const float* i0 = vin + y0 * rs + k1;
+    const float* i1 = i0 + rs;
     float s0[G::AX2], s1[G::AX2];
     sfor<0, G::AX2>([&](auto K2) {
       constexpr int k2 = decltype(K2)::value;
-      s0[k2] = v0p[G::AX1 * k2];
-      s1[k2] = has1 ? v1p[G::AX1 * k2] : 0.f;
+      s0[k2] = i0[G::AX1 * k2];
+      s1[k2] = has1 ? i1[G::AX1 * k2] : 0.f;
     });
     float2 z[G::AX2];
     const float2* r = S + p * G::PST + k1 * G::PA;
@@ -281,19 +318,21 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
 // component also p = c0^2 (rho_x + rho_y + rho_z), written as pairs to pout.
 template <class G, bool LAST>
 __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, float* __restrict__ rho,
-                                               const float* __restrict__ lam, int comp, float lz,
-                                               float dtr0, const float* rx, const float* rz,
-                                               const float* __restrict__ c2) {
+                                               const float* rin, int rs, const float* __restrict__ lam,
+                                               int comp, float lz, float dtr0, const float* rx,
+                                               const float* rz, const float* __restrict__ c2) {
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
     const int p = t / G::AX1, k1 = t - p * G::AX1;
     const int y0 = 2 * p, y1 = y0 + 1;
     const bool has1 = y1 < G::NYc;
     const int o0 = y0 * G::NXc + k1, o1 = o0 + G::NXc;
+    const float* i0 = rin + y0 * rs + k1;
+    const float* i1 = i0 + rs;
     float s0[G::AX2], s1[G::AX2];
     sfor<0, G::AX2>([&](auto K2) {
       constexpr int k2 = decltype(K2)::value;
-      s0[k2] = rho[o0 + G::AX1 * k2];
-      s1[k2] = has1 ? rho[o1 + G::AX1 * k2] : 0.f;
+      s0[k2] = i0[G::AX1 * k2];
+      s1[k2] = has1 ? i1[G::AX1 * k2] : 0.f;
     });
     float2 z[G::AX2];
     const float2* r = S + p * G::PST + k1 * G::PA;
@@ -338,40 +377,48 @@ template <int NX, int NY>
 __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mom(const __grid_constant__ StepParams P) {
   using G = Plane2<NX, NY>;
   if (*P.bad) return;
-  extern __shared__ float2 sm2[];
+  extern __shared__ __align__(16) float2 sm2[];
   const float2* twx = sm2;
   const float2* twxT = sm2 + NX;
   const float2* twy = sm2 + 2 * NX;
-  float2* S = sm2 + G::TW;
+  float2* S = sm2 + G::TWP;
   float2* X = S + G::NP * G::PST;
-  p2_stage_twiddles<G>(sm2, P);
-  __syncthreads();
+  float2* Gb = X + G::NP * G::PST;      // staging buffer (when G::STAGE)
   const int z = blockIdx.x;
   const SimPtrs& Q = P.sims[blockIdx.y];
   const size_t soff = (size_t)z * (G::HX * NY);
   const size_t voff = (size_t)z * (NX * NY);
   // component order z, x, y: R -> V_z (spec[1]), Q -> V_x (spec[2]), Q -> V_y (spec[0])
+  auto src_of = [&](int comp) { return (comp == 2 ? Q.spec[1] : Q.spec[0]) + soff; };
+  if constexpr (G::STAGE) p2_fetch_spec<G>(Gb, src_of(2));
+  p2_stage_twiddles<G>(sm2, P);
+  const float lz = __ldg(&P.lams[2][z]);
 #pragma unroll 1
   for (int cc = 0; cc < 3; ++cc) {
     const int comp = cc == 0 ? 2 : cc - 1;
-    const float2* src = (comp == 2 ? Q.spec[1] : Q.spec[0]) + soff;
     float2* dst = (comp == 2 ? Q.spec[1] : (comp == 0 ? Q.spec[2] : Q.spec[0])) + soff;
-    const float lz = __ldg(&P.lams[2][z]);
-    p2_yinv_a<G>(S, src, comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.ap[comp], twy);
+    float* vg = Q.v[comp] + voff;
+    if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
+    p2_yinv_a<G>(S, G::STAGE ? Gb : src_of(comp), comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.ap[comp], twy);
+    __syncthreads();
+    if constexpr (G::STAGE) p2_fetch_rows<G>(Gb, vg);      // overlaps phases 2 and 3
     p2_y_b<G, true>(S, X, nullptr);
     __syncthreads();
     p2_xinv_a<G>(X, S, twx);
+    if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
-    p2_mom_update<G>(S, X, twxT, Q.v[comp] + voff, P.lams[comp], comp, lz, P.dt_over_rho0);
+    p2_mom_update<G>(S, X, twxT, vg, G::STAGE ? reinterpret_cast<const float*>(Gb) : vg,
+                     G::STAGE ? G::RS : NX, P.lams[comp], comp, lz, P.dt_over_rho0);
     __syncthreads();
+    if constexpr (G::STAGE) {                               // next spectrum overlaps phases 5-7
+      if (cc < 2) p2_fetch_spec<G>(Gb, src_of(cc == 0 ? 0 : 1));
+    }
     p2_xfwd_b<G>(X, S);
     __syncthreads();
     p2_yfwd_a<G>(S, X, twy);
     __syncthreads();
     p2_y_b<G, false>(X, nullptr, dst);
-    // the next component writes S (last read before the previous barrier) and reads
-    // a global plane this component does not write
   }
 }
 
@@ -379,43 +426,50 @@ template <int NX, int NY>
 __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __grid_constant__ StepParams P) {
   using G = Plane2<NX, NY>;
   if (*P.bad) return;
-  extern __shared__ float2 sm2[];
+  extern __shared__ __align__(16) float2 sm2[];
   const float2* twx = sm2;
   const float2* twxT = sm2 + NX;
   const float2* twy = sm2 + 2 * NX;
-  float2* S = sm2 + G::TW;
+  float2* S = sm2 + G::TWP;
   float2* X = S + G::NP * G::PST;
-  p2_stage_twiddles<G>(sm2, P);
-  __syncthreads();
+  float2* Gb = X + G::NP * G::PST;      // staging buffer (when G::STAGE)
   const int z = blockIdx.x;
   const SimPtrs& Q = P.sims[blockIdx.y];
   const int role = Q.role, shot = Q.shot, tix = P.tidx[blockIdx.y];
   const size_t soff = (size_t)z * (G::HX * NY);
   const size_t voff = (size_t)z * (NX * NY);
   const float lz = __ldg(&P.lam[2][z]);
-  // component order x (spec[2]), z (spec[1]), y (spec[0]); the last one assembles p
+  // component order x (spec[2]), z (spec[1]), y (spec[0]); the last one assembles p.
+  // Spectra of the second and third components are staged in X, which is free from
+  // the end of phase 3 to the next phase 2; rho rows in the staging buffer.
+  if constexpr (G::STAGE) p2_fetch_spec<G>(Gb, Q.spec[2] + soff);
+  p2_stage_twiddles<G>(sm2, P);
 #pragma unroll 1
-  for (int cc = 0; cc < 2; ++cc) {
-    const int comp = cc == 0 ? 0 : 2;
-    const float2* src = (comp == 0 ? Q.spec[2] : Q.spec[1]) + soff;
-    p2_yinv_a<G>(S, src, comp == 0 ? 1 : 0, P.am[comp], twy);
+  for (int cc = 0; cc < 3; ++cc) {
+    const int comp = cc == 0 ? 0 : (cc == 1 ? 2 : 1);
+    float* rg = Q.rho[comp] + voff;
+    const float2* src = cc == 0 ? (G::STAGE ? Gb : Q.spec[2] + soff) : X;
+    cp_async_wait_all();
     __syncthreads();
+    p2_yinv_a<G>(S, src, comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.am[comp], twy);
+    __syncthreads();
+    if constexpr (G::STAGE) p2_fetch_rows<G>(Gb, rg);      // overlaps phases 2 and 3
     p2_y_b<G, true>(S, X, nullptr);
     __syncthreads();
     p2_xinv_a<G>(X, S, twx);
+    if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
-    p2_mass_update<G, false>(S, nullptr, Q.rho[comp] + voff, P.lam[comp], comp, lz, P.dt_rho0, nullptr,
-                             nullptr, nullptr);
-    __syncthreads();
+    const float* rin = G::STAGE ? reinterpret_cast<const float*>(Gb) : rg;
+    const int rs = G::STAGE ? G::RS : NX;
+    if (cc < 2) {
+      p2_fetch_spec<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff);   // overlaps phase 4
+      p2_mass_update<G, false>(S, nullptr, rg, rin, rs, P.lam[comp], comp, lz, P.dt_rho0, nullptr, nullptr,
+                               nullptr);
+    } else {
+      p2_mass_update<G, true>(S, X, rg, rin, rs, P.lam[1], 1, lz, P.dt_rho0, Q.rho[0] + voff,
+                              Q.rho[2] + voff, P.c2 + voff);
+    }
   }
-  p2_yinv_a<G>(S, Q.spec[0] + soff, 2, P.am[1], twy);
-  __syncthreads();
-  p2_y_b<G, true>(S, X, nullptr);
-  __syncthreads();
-  p2_xinv_a<G>(X, S, twx);
-  __syncthreads();
-  p2_mass_update<G, true>(S, X, Q.rho[1] + voff, P.lam[1], 1, lz, P.dt_rho0, Q.rho[0] + voff,
-                          Q.rho[2] + voff, P.c2 + voff);
   __syncthreads();
   // sparse updates of rho_xi and p on this plane, then recording
   const int key0 = z * G::NP, key1 = key0 + G::NP;
@@ -530,19 +584,28 @@ __global__ void __launch_bounds__(Z2<NZ, TZ>::NT) k_zpass2(const __grid_constant
   const int m0 = blockIdx.x * TZ;
   const float rhx = 1.0f / (float)P.hx;
   const int nslot = MODE == 0 ? 1 : 3;
+  auto src_of = [&](int s) {
+    return MODE == 0 ? Q.spec[0] : (s == 0 ? Q.spec[2] : (s == 1 ? Q.spec[0] : Q.spec[1]));
+  };
+  // forward step A inputs of this thread (column m0 + ml, rows j2 + N2 j1); the next
+  // slot's are loaded before the current slot's step B (software pipelining)
+  const int mlA = threadIdx.x % TZ, j2A = threadIdx.x / TZ;
+  float2 a[N1];
+  auto load_a = [&](int s) {
+    const float2* src = src_of(s);
+    const int m = m0 + mlA;
+    sfor<0, N1>([&](auto J1) {
+      constexpr int j1 = decltype(J1)::value;
+      a[j1] = m < M ? __ldg(&src[(size_t)(j2A + N2 * j1) * M + m]) : make_float2(0.f, 0.f);
+    });
+  };
+  load_a(0);
 #pragma unroll 1
   for (int s = 0; s < nslot; ++s) {
-    const float2* src = MODE == 0 ? Q.spec[0] : (s == 0 ? Q.spec[2] : (s == 1 ? Q.spec[0] : Q.spec[1]));
     __syncthreads();   // twiddles staged; previous slot's buffers consumed
-    // forward step A: DFT_N1 of x[j2 + N2 j1] from global, twiddle -> b0
+    // forward step A: DFT_N1 of x[j2 + N2 j1], twiddle -> b0
     {
-      const int ml = threadIdx.x % TZ, j2 = threadIdx.x / TZ;
-      const int m = m0 + ml;
-      float2 a[N1];
-      sfor<0, N1>([&](auto J1) {
-        constexpr int j1 = decltype(J1)::value;
-        a[j1] = m < M ? __ldg(&src[(size_t)(j2 + N2 * j1) * M + m]) : make_float2(0.f, 0.f);
-      });
+      const int ml = mlA, j2 = j2A;
       RDft<N1, false>::run(a);
       sfor<0, N1>([&](auto K1) {
         constexpr int k1 = decltype(K1)::value;
@@ -550,6 +613,7 @@ __global__ void __launch_bounds__(Z2<NZ, TZ>::NT) k_zpass2(const __grid_constant
       });
     }
     __syncthreads();
+    if (MODE == 1 && s + 1 < nslot) load_a(s + 1);
     // forward step B, kappa, inverse step A (per output) -> b1 (, b2)
     for (int t = threadIdx.x; t < TZ * N1; t += C::NT) {
       const int ml = t % TZ, k1 = t / TZ;
