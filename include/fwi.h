@@ -153,9 +153,10 @@ int64_t fwi_plan_launches(const fwi_plan *plan, int32_t K, int32_t gradient);
  * FFT schedule of a plan (what the autotuner searches).
  *   specialized: 1 = compile-time transforms where this build has them (square planes
  *                of 32, 64, 96, 128, 160; z lengths 32..128), 0 = runtime schedules,
- *                2 = as 1, with the xy work done by the two-step register-transform
- *                plane kernels (square planes of 32, 64, 96, 128, 135, 160 only;
- *                FWI_ENOTSUP for other planes)
+ *                2 = two-step register-transform kernels where this build has them:
+ *                whole square planes of 32, 64, 96, 128, 135, 160; split square planes of
+ *                243, 256, 480; z lengths 32, 48, 64, 80, 96, 128, 135, 256 (the other
+ *                passes as for 1; FWI_ENOTSUP when none applies)
  *   radix_order: runtime radix schedule: 0 = radix 8, 4, 2 then 3, 5; 1 = radix 4, 2
  *                then 3, 5 (no radix 8); 2 = small radices first (2, 3, 4, 5, 8 order
  *                reversed: the largest pass last)
@@ -163,8 +164,8 @@ int64_t fwi_plan_launches(const fwi_plan *plan, int32_t K, int32_t gradient);
  *   split_plane: 0 = one CTA transforms a whole z-plane in shared memory; 1 = the XY
  *                work of a plane is split into column (y) and row-pair (x) passes
  *                through global memory (always used when a plane does not fit)
- * fwi_plan_create picks {2, 0, 32, 0} where the two-step plane kernels are built, else
- * {1, 0, 32, 0}, else {1, 0, 32, 1} (the plane does not fit).  Setting a schedule keeps the workspace size;
+ * fwi_plan_create picks the first of {2, 0, 32, 0}, {2, 0, 32, 1}, {1, 0, 32, 0}, {1, 0, 32, 1}
+ * that applies (split planes only where a plane does not fit).  Setting a schedule keeps the workspace size;
  * it may be changed after binding (between calls).  Results differ only by FP32
  * rounding order.  Errors: FWI_EINVAL (bad values), FWI_ENOTSUP (the shared memory
  * the schedule needs exceeds the device limit).

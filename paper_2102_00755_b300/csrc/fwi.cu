@@ -15,6 +15,7 @@
 #include "../../include/fwi.h"
 #include "kernels.cuh"
 #include "plane2.cuh"
+#include "split2.cuh"
 
 using namespace fwi;
 
@@ -269,6 +270,8 @@ struct fwi_plan {
   size_t smem_p2;
   int z2;    // nz of the two-step register-transform z pass (0: not used)
   size_t smem_z2[2];
+  int s2;    // plane side of the two-step split-plane kernels (0: not used)
+  size_t smem_y2, smem_x2;
   int fz;    // specialised z length (0: runtime schedules)
   int tz;    // z-pass tile width (columns)
   int split; // XY work split into column and row-pair passes (large planes)
@@ -337,6 +340,11 @@ void base_params(fwi_plan* p, StepParams* P) {
     P->lams[c] = at<float>(p, p->o_lams[c]);
   }
   P->half_cdt = (float)(q.c_ref * q.dt / 2.0);
+  {
+    // largest argument c_ref dt |k| / 2 of the sinc in kappa (Eq. 18): |k_xi| <= pi / dx
+    const double amax = q.c_ref * q.dt / 2.0 * std::sqrt(3.0) * M_PI / q.dx;
+    P->kappa_series = amax <= 3.1 ? 1 : 0;
+  }
   P->inv_n = (float)(1.0 / (double)p->nvox);
   P->dt_over_rho0 = (float)(q.dt / q.rho0);
   P->dt_rho0 = (float)(q.dt * q.rho0);
@@ -421,6 +429,17 @@ fwi_status cuda_fail(cudaError_t e, const char* what) {
     case 256: { constexpr int NZ = 256; CALL; } break;                  \
     default: break;                                                     \
   }
+// split planes: y-pass columns per CTA (8 where the 27-point step B needs the register
+// file of a smaller CTA) and x-pass row pairs per CTA
+__host__ __device__ constexpr int ty2_for(int n) { return n / split_n1(n) > 16 ? 8 : 16; }
+constexpr int kNPC2 = 8;
+#define S2_DISPATCH(p, CALL)                                            \
+  switch ((p)->s2) {                                                    \
+    case 243: { constexpr int N = 243; CALL; } break;                   \
+    case 256: { constexpr int N = 256; CALL; } break;                   \
+    case 480: { constexpr int N = 480; CALL; } break;                   \
+    default: break;                                                     \
+  }
 #define Z2_DISPATCH(p, CALL)                                            \
   if ((p)->tz == 32) { constexpr int TZ = 32; Z2_DISPATCH_T(p, TZ, CALL) } \
   else { constexpr int TZ = 16; Z2_DISPATCH_T(p, TZ, CALL) }
@@ -462,6 +481,15 @@ void set_attrs_p2(int cap) {
   cudaFuncSetAttribute(k_plane2_mom<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_plane2_mass<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
+template <int N>
+void set_attrs_s2(int cap) {
+  cudaFuncSetAttribute(k_ypass2<Y_INV_MOM, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_ypass2<Y_INV_MASS, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_ypass2<Y_FWD3, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_ypass2<Y_FWD1, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_xpass2_mom<N, kNPC2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_xpass2_mass<N, kNPC2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
 template <int NZ, int TZ>
 void set_attrs_z2(int cap) {
   cudaFuncSetAttribute(k_zpass2<0, NZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
@@ -490,6 +518,7 @@ void set_attrs(fwi_plan* p) {
   PLANE_DISPATCH(p, (set_attrs_plane<E, F>(cap)));
   P2_DISPATCH(p, (set_attrs_p2<N>(cap)));
   Z2_DISPATCH(p, (set_attrs_z2<NZ, TZ>(cap)));
+  S2_DISPATCH(p, (set_attrs_s2<N>(cap)));
   Z_DISPATCH(p, (set_attrs_z<E, FZ, TZ>(cap)));
   // Touch every small kernel too, so that modules are loaded before any stream
   // capture of a call (a first launch inside a capture may not load them).
@@ -526,6 +555,9 @@ fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   const int warps = kTpbPlane / 32;
   const dim3 gx1((p->npair + warps * g1 - 1) / (warps * g1), p->prob.nz, P.nsims);
   const dim3 gx2((p->npair + warps * g2 - 1) / (warps * g2), p->prob.nz, P.nsims);
+  const int ty2 = ty2_for(p->s2 > 0 ? p->s2 : 1);
+  const dim3 gy2((p->hx + ty2 - 1) / ty2, p->prob.nz, P.nsims);
+  const dim3 gx2b((p->npair + kNPC2 - 1) / kNPC2, p->prob.nz, P.nsims);
   int slot;
   prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
   if (p->z2) {
@@ -537,12 +569,21 @@ fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
-  k_ypass<Y_INV_MOM, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
-  LAUNCHED("k_ypass<inverse, momentum>");
-  k_xpass_mom<EL><<<gx1, kTpbPlane, p->smem_xmom, st>>>(P);
-  LAUNCHED("k_xpass_mom");
-  k_ypass<Y_FWD3, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
-  LAUNCHED("k_ypass<forward x3>");
+  if (p->s2) {
+    S2_DISPATCH(p, (k_ypass2<Y_INV_MOM, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
+    LAUNCHED("k_ypass2<inverse, momentum>");
+    S2_DISPATCH(p, (k_xpass2_mom<N, kNPC2><<<gx2b, X2<N, kNPC2>::NT, p->smem_x2, st>>>(P)));
+    LAUNCHED("k_xpass2_mom");
+    S2_DISPATCH(p, (k_ypass2<Y_FWD3, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
+    LAUNCHED("k_ypass2<forward x3>");
+  } else {
+    k_ypass<Y_INV_MOM, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
+    LAUNCHED("k_ypass<inverse, momentum>");
+    k_xpass_mom<EL><<<gx1, kTpbPlane, p->smem_xmom, st>>>(P);
+    LAUNCHED("k_xpass_mom");
+    k_ypass<Y_FWD3, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
+    LAUNCHED("k_ypass<forward x3>");
+  }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
   if (p->z2) {
@@ -554,12 +595,21 @@ fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
-  k_ypass<Y_INV_MASS, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
-  LAUNCHED("k_ypass<inverse, mass>");
-  k_xpass_mass<EL><<<gx2, kTpbPlane, p->smem_xmass, st>>>(P);
-  LAUNCHED("k_xpass_mass");
-  k_ypass<Y_FWD1, EL><<<gy, kTpbZ, p->smem_ypass1, st>>>(P);
-  LAUNCHED("k_ypass<forward x1>");
+  if (p->s2) {
+    S2_DISPATCH(p, (k_ypass2<Y_INV_MASS, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
+    LAUNCHED("k_ypass2<inverse, mass>");
+    S2_DISPATCH(p, (k_xpass2_mass<N, kNPC2><<<gx2b, X2<N, kNPC2>::NT, p->smem_x2, st>>>(P)));
+    LAUNCHED("k_xpass2_mass");
+    S2_DISPATCH(p, (k_ypass2<Y_FWD1, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
+    LAUNCHED("k_ypass2<forward x1>");
+  } else {
+    k_ypass<Y_INV_MASS, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
+    LAUNCHED("k_ypass<inverse, mass>");
+    k_xpass_mass<EL><<<gx2, kTpbPlane, p->smem_xmass, st>>>(P);
+    LAUNCHED("k_xpass_mass");
+    k_ypass<Y_FWD1, EL><<<gy, kTpbZ, p->smem_ypass1, st>>>(P);
+    LAUNCHED("k_ypass<forward x1>");
+  }
   prof_end(p, st, slot);
   return FWI_OK;
 }
@@ -645,6 +695,8 @@ fwi_status apply_schedule(fwi_plan* p) {
   p->smem_p2 = 0;
   p->z2 = 0;
   p->smem_z2[0] = p->smem_z2[1] = 0;
+  p->s2 = 0;
+  p->smem_y2 = p->smem_x2 = 0;
   if (sc.specialized == 2) {   // two-step kernels where built (planes, z pass or both)
     if (!p->split && q.nx == q.ny && in(q.nx, {32, 64, 96, 128, 135, 160})) {
       p->p2 = q.nx;
@@ -656,7 +708,12 @@ fwi_status apply_schedule(fwi_plan* p) {
       Z2_DISPATCH(p, (p->smem_z2[0] = Z2<NZ, TZ>::smem(0), p->smem_z2[1] = Z2<NZ, TZ>::smem(1)));
       if (p->smem_z2[0] > 227 * 1024) p->z2 = 0;
     }
-    if (!p->p2 && !p->z2) return FWI_ENOTSUP;
+    if (p->split && q.nx == q.ny && in(q.nx, {243, 256, 480})) {
+      p->s2 = q.nx;
+      S2_DISPATCH(p, (p->smem_y2 = Y2<N, ty2_for(N)>::SMEM, p->smem_x2 = X2<N, kNPC2>::SMEM));
+      if (p->smem_y2 > 227 * 1024 || p->smem_x2 > 227 * 1024) p->s2 = 0;
+    }
+    if (!p->p2 && !p->z2 && !p->s2) return FWI_ENOTSUP;
   }
   const int tw_x = p->ax.tw_off, tw_y = p->ay.tw_off, tw_z = p->az.tw_off;
   if (!factor235(q.nx, &p->ax, sc.radix_order) || !factor235(q.ny, &p->ay, sc.radix_order) ||
@@ -869,10 +926,11 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   }
 
   // launch shapes: every axis must fit one warp group (n <= 512)
-  // default schedule: two-step plane kernels where built, else the compile-time or
-  // runtime transforms, else (the plane does not fit one CTA) the split planes
+  // default schedule: two-step kernels where built (whole planes, else split planes),
+  // else the compile-time or runtime transforms (whole planes, else split planes)
   bool placed = false;
-  for (const fwi_schedule sc : {fwi_schedule{2, 0, 32, 0}, fwi_schedule{1, 0, 32, 0}, fwi_schedule{1, 0, 32, 1}}) {
+  for (const fwi_schedule sc : {fwi_schedule{2, 0, 32, 0}, fwi_schedule{2, 0, 32, 1}, fwi_schedule{1, 0, 32, 0},
+                                fwi_schedule{1, 0, 32, 1}}) {
     p->sched = sc;
     if (apply_schedule(p) == FWI_OK) {
       placed = true;

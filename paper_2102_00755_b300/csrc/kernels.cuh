@@ -70,6 +70,7 @@ struct StepParams {
   const float2* ap[3]; // a+_xi: i k exp(+i k dx/2), [hx], [ny], [nz]
   const float2* am[3]; // a-_xi
   float half_cdt;      // c_ref dt / 2
+  int kappa_series;    // 1: c_ref dt |k| / 2 <= 3.1 everywhere, kappa from the sinc series in s = a^2
   float inv_n;         // 1 / (nx ny nz)
   // PML (1D)
   const float* lam[3];

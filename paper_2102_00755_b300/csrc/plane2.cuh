@@ -273,21 +273,28 @@ __device__ __forceinline__ void p2_yfwd_a(const float2* in, float2* out, const f
 template <class G>
 __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, const float2* twxT,
                                               float* __restrict__ v, const float* vin, int rs,
-                                              const float* __restrict__ lam, int comp, float lz, float dtr) {
+                                              const float* __restrict__ lam, int comp, float lz, float dtr,
+                                              int nyl) {
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
     const int p = t / G::AX1, k1 = t - p * G::AX1;
     const int y0 = 2 * p, y1 = y0 + 1;
-    const bool has1 = y1 < G::NYc;
+    if (y0 >= nyl) continue;
+    const bool has1 = y1 < nyl;
     float* v0p = v + y0 * G::NXc + k1;
     float* v1p = v0p + G::NXc;
     const float* i0 = vin + y0 * rs + k1;
     const float* i1 = i0 + rs;
-    float s0[G::AX2], s1[G::AX2];
-    sfor<0, G::AX2>([&](auto K2) {
-      constexpr int k2 = decltype(K2)::value;
-      s0[k2] = i0[G::AX1 * k2];
-      s1[k2] = has1 ? i1[G::AX1 * k2] : 0.f;
-    });
+    // the old field is loaded ahead of the transform unless that would hold too many
+    // registers (long step-B lines)
+    constexpr bool PRE = G::AX2 <= 16;
+    float s0[PRE ? G::AX2 : 1], s1[PRE ? G::AX2 : 1];
+    if constexpr (PRE) {
+      sfor<0, G::AX2>([&](auto K2) {
+        constexpr int k2 = decltype(K2)::value;
+        s0[k2] = i0[G::AX1 * k2];
+        s1[k2] = has1 ? i1[G::AX1 * k2] : 0.f;
+      });
+    }
     float2 z[G::AX2];
     const float2* r = S + p * G::PST + k1 * G::PA;
     sfor<0, G::AX2>([&](auto J) { z[decltype(J)::value] = r[decltype(J)::value]; });
@@ -301,11 +308,14 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
       constexpr int k2 = decltype(K2)::value;
       float a0 = l0, a1 = l1;
       if (comp == 0) a0 = a1 = __ldg(&lam[k1 + G::AX1 * k2]);
-      const float n0 = a0 * (a0 * s0[k2] - dtr * z[k2].x);
+      float o0v, o1v;
+      if constexpr (PRE) { o0v = s0[k2]; o1v = s1[k2]; }
+      else { o0v = i0[G::AX1 * k2]; o1v = has1 ? i1[G::AX1 * k2] : 0.f; }
+      const float n0 = a0 * (a0 * o0v - dtr * z[k2].x);
       v0p[G::AX1 * k2] = n0;
       float n1 = 0.f;
       if (has1) {
-        n1 = a1 * (a1 * s1[k2] - dtr * z[k2].y);
+        n1 = a1 * (a1 * o1v - dtr * z[k2].y);
         v1p[G::AX1 * k2] = n1;
       }
       z[k2] = make_float2(n0, n1);
@@ -320,20 +330,24 @@ template <class G, bool LAST>
 __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, float* __restrict__ rho,
                                                const float* rin, int rs, const float* __restrict__ lam,
                                                int comp, float lz, float dtr0, const float* rx,
-                                               const float* rz, const float* __restrict__ c2) {
+                                               const float* rz, const float* __restrict__ c2, int nyl) {
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
     const int p = t / G::AX1, k1 = t - p * G::AX1;
     const int y0 = 2 * p, y1 = y0 + 1;
-    const bool has1 = y1 < G::NYc;
+    if (y0 >= nyl) continue;
+    const bool has1 = y1 < nyl;
     const int o0 = y0 * G::NXc + k1, o1 = o0 + G::NXc;
     const float* i0 = rin + y0 * rs + k1;
     const float* i1 = i0 + rs;
-    float s0[G::AX2], s1[G::AX2];
-    sfor<0, G::AX2>([&](auto K2) {
-      constexpr int k2 = decltype(K2)::value;
-      s0[k2] = i0[G::AX1 * k2];
-      s1[k2] = has1 ? i1[G::AX1 * k2] : 0.f;
-    });
+    constexpr bool PRE = G::AX2 <= 16;   // as in the momentum update
+    float s0[PRE ? G::AX2 : 1], s1[PRE ? G::AX2 : 1];
+    if constexpr (PRE) {
+      sfor<0, G::AX2>([&](auto K2) {
+        constexpr int k2 = decltype(K2)::value;
+        s0[k2] = i0[G::AX1 * k2];
+        s1[k2] = has1 ? i1[G::AX1 * k2] : 0.f;
+      });
+    }
     float2 z[G::AX2];
     const float2* r = S + p * G::PST + k1 * G::PA;
     sfor<0, G::AX2>([&](auto J) { z[decltype(J)::value] = r[decltype(J)::value]; });
@@ -349,11 +363,14 @@ __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, fl
       constexpr int xo = G::AX1 * k2;
       float a0 = l0, a1 = l1;
       if (comp == 0) a0 = a1 = __ldg(&lam[k1 + xo]);
-      const float r0 = a0 * (a0 * s0[k2] - dtr0 * z[k2].x);
+      float o0v, o1v;
+      if constexpr (PRE) { o0v = s0[k2]; o1v = s1[k2]; }
+      else { o0v = i0[xo]; o1v = has1 ? i1[xo] : 0.f; }
+      const float r0 = a0 * (a0 * o0v - dtr0 * z[k2].x);
       rho[o0 + xo] = r0;
       float r1 = 0.f;
       if (has1) {
-        r1 = a1 * (a1 * s1[k2] - dtr0 * z[k2].y);
+        r1 = a1 * (a1 * o1v - dtr0 * z[k2].y);
         rho[o1 + xo] = r1;
       }
       if (LAST) {
@@ -409,7 +426,7 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mom(const __gr
     if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
     p2_mom_update<G>(S, X, twxT, vg, G::STAGE ? reinterpret_cast<const float*>(Gb) : vg,
-                     G::STAGE ? G::RS : NX, P.lams[comp], comp, lz, P.dt_over_rho0);
+                     G::STAGE ? G::RS : NX, P.lams[comp], comp, lz, P.dt_over_rho0, NY);
     __syncthreads();
     if constexpr (G::STAGE) {                               // next spectrum overlaps phases 5-7
       if (cc < 2) p2_fetch_spec<G>(Gb, src_of(cc == 0 ? 0 : 1));
@@ -464,10 +481,10 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
     if (cc < 2) {
       p2_fetch_spec<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff);   // overlaps phase 4
       p2_mass_update<G, false>(S, nullptr, rg, rin, rs, P.lam[comp], comp, lz, P.dt_rho0, nullptr, nullptr,
-                               nullptr);
+                               nullptr, NY);
     } else {
       p2_mass_update<G, true>(S, X, rg, rin, rs, P.lam[1], 1, lz, P.dt_rho0, Q.rho[0] + voff,
-                              Q.rho[2] + voff, P.c2 + voff);
+                              Q.rho[2] + voff, P.c2 + voff, NY);
     }
   }
   __syncthreads();
@@ -552,10 +569,34 @@ namespace fwi {
 //   -> global.
 // MODE 0 (momentum): spec[0] -> Q (spec[0]) and R = Q a+_z (spec[1]).
 // MODE 1 (mass): spec[2] (x), spec[0] (y), spec[1] (z, times a-_z), in place.
+// kappa(k) / N = sinc(c_ref dt |k| / 2) / N (Eq. 18).  For arguments a <= 3.1 the sinc is
+// the Taylor series of sin(a)/a, sum (-1)^n a^(2n) / (2n+1)!, truncated after a^18 (error
+// below 2e-10 there) and evaluated by Horner's rule in s = a^2 = (c_ref dt / 2)^2 |k|^2:
+// no square root, sine or division.  Otherwise sinf(a) / a.
+__device__ __forceinline__ float kappa_over_n(float kk, const StepParams& P) {
+  if (P.kappa_series) {
+    const float s = P.half_cdt * P.half_cdt * kk;
+    float r = -1.0f / 121645100408832000.0f;                 // -1/19!
+    r = fmaf(r, s, 1.0f / 355687428096000.0f);               //  1/17!
+    r = fmaf(r, s, -1.0f / 1307674368000.0f);                // -1/15!
+    r = fmaf(r, s, 1.0f / 6227020800.0f);                    //  1/13!
+    r = fmaf(r, s, -1.0f / 39916800.0f);                     // -1/11!
+    r = fmaf(r, s, 1.0f / 362880.0f);                        //  1/9!
+    r = fmaf(r, s, -1.0f / 5040.0f);                         // -1/7!
+    r = fmaf(r, s, 1.0f / 120.0f);                           //  1/5!
+    r = fmaf(r, s, -1.0f / 6.0f);                            // -1/3!
+    r = fmaf(r, s, 1.0f);
+    return r * P.inv_n;
+  }
+  const float a = P.half_cdt * sqrtf(kk);
+  return (a > 0.f ? sinf(a) / a : 1.f) * P.inv_n;
+}
+
 template <int NZ, int TZ>
 struct Z2 {
   static constexpr int N1 = split_n1(NZ), N2 = NZ / N1;
   static constexpr int NT = TZ * N2;                 // forward step A: one task per thread
+  static_assert(N1 <= N2, "step B runs one task per thread on the first TZ * N1 threads");
   static constexpr int TW = NZ + NZ;                 // W_NZ^e and the transposed table
   static constexpr size_t smem(int mode) { return (size_t)(TW + (mode == 0 ? 3 : 2) * NZ * TZ) * 8; }
 };
@@ -600,6 +641,21 @@ __global__ void __launch_bounds__(Z2<NZ, TZ>::NT) k_zpass2(const __grid_constant
     });
   };
   load_a(0);
+  // kappa / N of this thread's step-B column and kz = k1 + N1 k2, shared by all slots
+  const bool hasB = threadIdx.x < TZ * N1;
+  const int mlB = threadIdx.x % TZ, k1B = threadIdx.x / TZ;
+  float kap[N2];
+  {
+    const int m = m0 + mlB;
+    const int mm = m < M ? m : M - 1;
+    const int ky = fdivi(mm, rhx);
+    const int kx = mm - ky * P.hx;
+    const float kxy = __ldg(&P.kx2[kx]) + __ldg(&P.ky2[ky]);
+    sfor<0, N2>([&](auto K2) {
+      constexpr int k2 = decltype(K2)::value;
+      kap[k2] = hasB ? kappa_over_n(kxy + __ldg(&P.kz2[k1B + N1 * k2]), P) : 0.f;
+    });
+  }
 #pragma unroll 1
   for (int s = 0; s < nslot; ++s) {
     __syncthreads();   // twiddles staged; previous slot's buffers consumed
@@ -615,23 +671,16 @@ __global__ void __launch_bounds__(Z2<NZ, TZ>::NT) k_zpass2(const __grid_constant
     __syncthreads();
     if (MODE == 1 && s + 1 < nslot) load_a(s + 1);
     // forward step B, kappa, inverse step A (per output) -> b1 (, b2)
-    for (int t = threadIdx.x; t < TZ * N1; t += C::NT) {
-      const int ml = t % TZ, k1 = t / TZ;
-      const int m = m0 + ml;
+    if (hasB) {
+      const int ml = mlB, k1 = k1B;
       float2 x[N2];
       sfor<0, N2>([&](auto J2) { x[decltype(J2)::value] = b0[(N2 * k1 + decltype(J2)::value) * TZ + ml]; });
       RDft<N2, false>::run(x);
-      const int mm = m < M ? m : M - 1;
-      const int ky = fdivi(mm, rhx);
-      const int kx = mm - ky * P.hx;
-      const float kxy = __ldg(&P.kx2[kx]) + __ldg(&P.ky2[ky]);
       float2 r[N2];
       sfor<0, N2>([&](auto K2) {
         constexpr int k2 = decltype(K2)::value;
         const int kz = k1 + N1 * k2;
-        const float a = P.half_cdt * sqrtf(kxy + __ldg(&P.kz2[kz]));
-        const float kap = (a > 0.f ? sinf(a) / a : 1.f) * P.inv_n;
-        const float2 v = cscale(x[k2], kap);
+        const float2 v = cscale(x[k2], kap[k2]);
         if constexpr (MODE == 0) {
           x[k2] = v;
           r[k2] = cmul(v, __ldg(&P.ap[2][kz]));

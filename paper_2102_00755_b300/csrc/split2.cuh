@@ -1,0 +1,334 @@
+// Split-plane XY work with two-step register transforms, for planes too large
+// for one CTA's shared memory (the 243^2 and 480^2 serving grids).  Each XY
+// half-step of Alg. 1 (App. B, Eqs. 18-19 in x and y) runs as
+//   k_ypass2   y transforms of TY adjacent kx columns of one z-plane, straight from
+//              and to global memory: step A reads, step B writes (one barrier);
+//   k_xpass2_* NPC row pairs of one z-plane: rows into shared memory, C2R packing
+//              and x-inverse step A, x-inverse step B with the field update and the
+//              forward x step A, forward step B, R2C unpacking to global rows.
+// The order per step matches the split path of kernels.cuh: zpass<MOM>,
+// ypass<INV_MOM>, xpass<MOM>, ypass<FWD3>, zpass<MASS>, ypass<INV_MASS>,
+// xpass<MASS>, ypass<FWD1>.
+#pragma once
+#include "plane2.cuh"
+
+namespace fwi {
+
+template <int NY, int TY>
+struct Y2 {
+  static constexpr int N1 = split_n1(NY), N2 = NY / N1;
+  static constexpr int NT = TY * N2;
+  static_assert(N1 <= N2, "step B runs on the first TY * N1 threads");
+  static constexpr size_t SMEM = (size_t)(NY + NY * TY) * 8;
+};
+
+template <int KIND, int NY, int TY>
+__global__ void __launch_bounds__(Y2<NY, TY>::NT) k_ypass2(const __grid_constant__ StepParams P) {
+  using C = Y2<NY, TY>;
+  constexpr int N1 = C::N1, N2 = C::N2;
+  constexpr bool INV = KIND == Y_INV_MOM || KIND == Y_INV_MASS;
+  constexpr int NSL = KIND == Y_FWD1 ? 1 : 3;
+  if (*P.bad) return;
+  extern __shared__ __align__(16) float2 ys2[];
+  float2* tw = ys2;
+  float2* b = ys2 + NY;
+  for (int i = threadIdx.x; i < NY; i += C::NT) tw[i] = P.tw[P.ay.tw_off + i];
+  const SimPtrs& S = P.sims[blockIdx.z];
+  const int HX = P.hx;
+  const size_t zoff = (size_t)blockIdx.y * P.mspec;
+  const int k0 = blockIdx.x * TY;
+  auto src_of = [&](int s) -> const float2* {
+    if (KIND == Y_INV_MOM) return s == 2 ? S.spec[1] : S.spec[0];
+    if (KIND == Y_FWD1) return S.spec[0];
+    return s == 0 ? S.spec[2] : (s == 1 ? S.spec[0] : S.spec[1]);
+  };
+  auto dst_of = [&](int s) -> float2* {
+    if (KIND == Y_INV_MOM) return s == 0 ? S.spec[2] : (s == 1 ? S.spec[0] : S.spec[1]);
+    return const_cast<float2*>(src_of(s));
+  };
+  // the y factor multiplies slot 1 of the inverse passes (a+_y: momentum, a-_y: mass)
+  const float2* fac = KIND == Y_INV_MOM ? P.ap[1] : P.am[1];
+  const int mlA = threadIdx.x % TY, j2A = threadIdx.x / TY;
+  const int kxA = k0 + mlA;
+  float2 a[N1];
+  auto load_a = [&](int s) {
+    const float2* src = src_of(s) + zoff;
+    sfor<0, N1>([&](auto J1) {
+      constexpr int j1 = decltype(J1)::value;
+      const int ky = j2A + N2 * j1;
+      float2 v = kxA < HX ? src[(size_t)ky * HX + kxA] : make_float2(0.f, 0.f);
+      if (INV && s == 1) v = cmul(v, __ldg(&fac[ky]));
+      a[j1] = v;
+    });
+  };
+  load_a(0);
+  const bool hasB = threadIdx.x < TY * N1;
+  const int mlB = threadIdx.x % TY, k1B = threadIdx.x / TY;
+  const int kxB = k0 + mlB;
+#pragma unroll 1
+  for (int s = 0; s < NSL; ++s) {
+    __syncthreads();   // twiddles staged; the previous slot's buffer consumed
+    if (N2 > 16 && s > 0) load_a(s);
+    RDft<N1, INV>::run(a);
+    sfor<0, N1>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      float2 v = a[k1];
+      if (k1 > 0) v = INV ? cmulc(v, tw[j2A * k1]) : cmul(v, tw[j2A * k1]);
+      b[(j2A + N2 * k1) * TY + mlA] = v;
+    });
+    __syncthreads();
+    if (N2 <= 16 && s + 1 < NSL) load_a(s + 1);   // in flight during step B (short lines)
+    if (hasB) {
+      float2 x[N2];
+      sfor<0, N2>([&](auto J2) { x[decltype(J2)::value] = b[(N2 * k1B + decltype(J2)::value) * TY + mlB]; });
+      RDft<N2, INV>::run(x);
+      if (kxB < HX) {
+        float2* dst = dst_of(s) + zoff;
+        sfor<0, N2>([&](auto K2) {
+          constexpr int k2 = decltype(K2)::value;
+          dst[(size_t)(k1B + N1 * k2) * HX + kxB] = x[k2];
+        });
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x passes over NPC row pairs of one z-plane
+template <int NX, int NPC>
+struct X2 {
+  static constexpr int NXc = NX, NPCc = NPC;
+  static constexpr int HX = NX / 2 + 1;
+  static constexpr int AX1 = split_n1(NX), AX2 = NX / AX1;
+  static constexpr int PA = AX2 + 1, PB = AX1 + 1;
+  static constexpr int PST = cmax3(2 * HX, AX1 * PA, AX2 * PB) | 1;
+  static constexpr int T3 = NPC * AX2, T4 = NPC * AX1, TU = NPC * HX;
+  static constexpr int NT = ((T3 > T4 ? T3 : T4) + 31) / 32 * 32;
+  static constexpr int TWP = (2 * NX + 1) & ~1;
+  static constexpr size_t SMEM = (size_t)(TWP + 2 * NPC * PST) * 8;
+};
+
+template <class G>
+__device__ __forceinline__ void x2_stage_twiddles(float2* tw, const StepParams& P) {
+  for (int i = threadIdx.x; i < 2 * G::NXc; i += G::NT) {
+    int e = i;
+    if (i >= G::NXc) {
+      const int t = i - G::NXc, k1p = t / G::AX1, j2p = t - k1p * G::AX1;
+      e = j2p * k1p;
+    }
+    tw[i] = P.tw[P.ax.tw_off + e];
+  }
+}
+
+// rows 2 p0 .. 2 p0 + 2 NPC - 1 (y < ny) of a spectrum plane -> pair regions of X
+template <class G>
+__device__ __forceinline__ void x2_load_rows(float2* X, const float2* __restrict__ src, int p0, int ny) {
+  for (int i = threadIdx.x; i < 2 * G::NPCc * G::HX; i += G::NT) {
+    const int r = i / G::HX, kx = i - r * G::HX;
+    const int y = 2 * p0 + r;
+    if (y < ny) cp_async8(&X[(r >> 1) * G::PST + (r & 1) * G::HX + kx], &src[(size_t)y * G::HX + kx]);
+  }
+  cp_async_commit();
+}
+
+// C2R packing (x factor applied to the half spectrum first) and x-inverse step A -> S
+template <class G>
+__device__ __forceinline__ void x2_xinv_a(const float2* X, float2* S, const float2* twx,
+                                          const float2* __restrict__ fac, int nyl) {
+  for (int t = threadIdx.x; t < G::T3; t += G::NT) {
+    const int j2 = t / G::NPCc, p = t - j2 * G::NPCc;
+    if (2 * p >= nyl) continue;
+    const float2* ra = X + p * G::PST;
+    const float2* rb = ra + G::HX;
+    const bool hasb = 2 * p + 1 < nyl;
+    float2 z[G::AX1];
+    sfor<0, G::AX1>([&](auto J1) {
+      constexpr int j1 = decltype(J1)::value;
+      const int k = j2 + G::AX2 * j1;
+      const bool mir = k >= G::HX;
+      const int kk = mir ? G::NXc - k : k;
+      float2 a = ra[kk], b = hasb ? rb[kk] : make_float2(0.f, 0.f);
+      if (fac) {
+        const float2 f = __ldg(&fac[kk]);
+        a = cmul(a, f);
+        b = cmul(b, f);
+      }
+      if (kk == 0 || 2 * kk == G::NXc) { a.y = 0.f; b.y = 0.f; }
+      if (mir) { a.y = -a.y; b.y = -b.y; }
+      z[j1] = make_float2(a.x - b.y, a.y + b.x);
+    });
+    RDft<G::AX1, true>::run(z);
+    sfor<1, G::AX1>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      z[k1] = cmulc(z[k1], twx[j2 * k1]);
+    });
+    float2* o = S + p * G::PST + j2;
+    sfor<0, G::AX1>([&](auto K1) { o[decltype(K1)::value * G::PA] = z[decltype(K1)::value]; });
+  }
+}
+
+// R2C unpacking of the pairs' Z (in) -> rows 2 p0 .. of a global spectrum plane
+template <class G>
+__device__ __forceinline__ void x2_unpack_store(const float2* in, float2* __restrict__ dst, int p0, int ny) {
+  for (int t = threadIdx.x; t < G::TU; t += G::NT) {
+    const int p = t / G::HX, kx = t - p * G::HX;
+    const int y0 = 2 * (p0 + p);
+    if (y0 >= ny) continue;
+    const float2* zp = in + p * G::PST;
+    const float2 zk = zp[kx], zm = zp[kx == 0 ? 0 : G::NXc - kx];
+    dst[(size_t)y0 * G::HX + kx] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    if (y0 + 1 < ny) dst[(size_t)(y0 + 1) * G::HX + kx] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+  }
+}
+
+// x work of the momentum half-step on split planes: components z (spec[1]), x (spec[2],
+// times a+_x), y (spec[0]); each: C2R, d+ p, v update with PML, R2C, back to its buffer
+template <int NX, int NPC>
+__global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mom(const __grid_constant__ StepParams P) {
+  using G = X2<NX, NPC>;
+  if (*P.bad) return;
+  extern __shared__ __align__(16) float2 xs2[];
+  const float2* twx = xs2;
+  const float2* twxT = xs2 + NX;
+  float2* S = xs2 + G::TWP;
+  float2* X = S + NPC * G::PST;
+  const int z = blockIdx.y;
+  const SimPtrs& Q = P.sims[blockIdx.z];
+  const int ny = P.ny, p0 = blockIdx.x * NPC;
+  const int nyl = min(2 * NPC, ny - 2 * p0);
+  const size_t soff = (size_t)z * P.mspec, voff = (size_t)z * P.plane + (size_t)(2 * p0) * NX;
+  auto buf_of = [&](int comp) { return (comp == 2 ? Q.spec[1] : (comp == 0 ? Q.spec[2] : Q.spec[0])) + soff; };
+  x2_load_rows<G>(X, buf_of(2), p0, ny);
+  x2_stage_twiddles<G>(xs2, P);
+  const float lz = __ldg(&P.lams[2][z]);
+#pragma unroll 1
+  for (int cc = 0; cc < 3; ++cc) {
+    const int comp = cc == 0 ? 2 : cc - 1;
+    float2* buf = buf_of(comp);
+    cp_async_wait_all();
+    __syncthreads();
+    x2_xinv_a<G>(X, S, twx, comp == 0 ? P.ap[0] : nullptr, nyl);
+    __syncthreads();
+    float* v = Q.v[comp] + voff;
+    p2_mom_update<G>(S, X, twxT, v, v, NX, comp == 1 ? P.lams[1] + 2 * p0 : P.lams[comp], comp, lz,
+                     P.dt_over_rho0, nyl);
+    __syncthreads();
+    p2_xfwd_b<G>(X, S);
+    __syncthreads();
+    if (cc < 2) x2_load_rows<G>(X, buf_of(cc == 0 ? 0 : 1), p0, ny);   // overlaps the stores
+    x2_unpack_store<G>(S, buf, p0, ny);
+  }
+}
+
+// x work of the mass half-step on split planes: components x (spec[2], times a-_x),
+// z (spec[1]), y (spec[0]); rho updates, p = c0^2 sum rho, sparse injection /
+// Dirichlet / recording on these pairs, R2C of p -> rows of spec[0]
+template <int NX, int NPC>
+__global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mass(const __grid_constant__ StepParams P) {
+  using G = X2<NX, NPC>;
+  if (*P.bad) return;
+  extern __shared__ __align__(16) float2 xs2[];
+  const float2* twx = xs2;
+  const float2* twxT = xs2 + NX;
+  float2* S = xs2 + G::TWP;
+  float2* X = S + NPC * G::PST;
+  const int z = blockIdx.y;
+  const SimPtrs& Q = P.sims[blockIdx.z];
+  const int role = Q.role, shot = Q.shot, tix = P.tidx[blockIdx.z];
+  const int ny = P.ny, p0 = blockIdx.x * NPC;
+  const int nyl = min(2 * NPC, ny - 2 * p0);
+  const int npl = (nyl + 1) / 2;
+  const size_t soff = (size_t)z * P.mspec, voff = (size_t)z * P.plane + (size_t)(2 * p0) * NX;
+  const float lz = __ldg(&P.lam[2][z]);
+  x2_load_rows<G>(X, Q.spec[2] + soff, p0, ny);
+  x2_stage_twiddles<G>(xs2, P);
+#pragma unroll 1
+  for (int cc = 0; cc < 3; ++cc) {
+    const int comp = cc == 0 ? 0 : (cc == 1 ? 2 : 1);
+    cp_async_wait_all();
+    __syncthreads();
+    x2_xinv_a<G>(X, S, twx, comp == 0 ? P.am[0] : nullptr, nyl);
+    __syncthreads();
+    float* rg = Q.rho[comp] + voff;
+    const float* lam = comp == 1 ? P.lam[1] + 2 * p0 : P.lam[comp];
+    if (cc < 2) {
+      x2_load_rows<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff, p0, ny);   // overlaps the update
+      p2_mass_update<G, false>(S, nullptr, rg, rg, NX, lam, comp, lz, P.dt_rho0, nullptr, nullptr, nullptr, nyl);
+    } else {
+      p2_mass_update<G, true>(S, X, rg, rg, NX, lam, comp, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
+                              P.c2 + voff, nyl);
+    }
+  }
+  __syncthreads();
+  // sparse updates of rho_xi and p on these pairs, then recording.  List offsets pf
+  // address pair regions of 2 hx complex of the whole plane; here pair p0 + q sits at
+  // region q of stride PST.
+  const int key0 = z * P.npair + p0, key1 = key0 + npl;
+  float* zf = reinterpret_cast<float*>(X);
+  auto loc = [&](int pf) {
+    const int q = pf / (4 * G::HX);
+    return pf + q * (2 * G::PST - 4 * G::HX) - p0 * 2 * G::PST;
+  };
+  if (role == ROLE_FORWARD) {
+    const float* amp = P.amp_src + ((size_t)shot * P.nt + tix) * P.n_us;
+    for (int u = P.us_ptr[key0] + threadIdx.x; u < P.us_ptr[key1]; u += G::NT) {
+      const int vx = P.us_vox[u];
+      const float a = amp[u];
+      Q.rho[0][vx] += a;
+      Q.rho[1][vx] += a;
+      Q.rho[2][vx] += a;
+      zf[loc(P.us_pf[u])] += P.c2[vx] * (3.f * a);
+    }
+  } else if (role == ROLE_ADJOINT) {
+    const float* q = P.qf + ((size_t)shot * P.nt + tix) * P.n_rec;
+    for (int u = P.ur_ptr[key0] + threadIdx.x; u < P.ur_ptr[key1]; u += G::NT) {
+      float s = 0.f;
+      for (int e = P.ur_mptr[u]; e < P.ur_mptr[u + 1]; ++e) s += q[P.ur_mem[e]];
+      const float a = P.ur_coef[u] * s;
+      const int vx = P.ur_vox[u];
+      Q.rho[0][vx] += a;
+      Q.rho[1][vx] += a;
+      Q.rho[2][vx] += a;
+      zf[loc(P.ur_pf[u])] += P.c2[vx] * (3.f * a);
+    }
+  } else {  // TR: rho_xi(layer) <- g^(Nt - m) / (3 c0^2)
+    const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1 - tix)) * P.n_layer;
+    for (int j = P.lay_ptr[key0] + threadIdx.x; j < P.lay_ptr[key1]; j += G::NT) {
+      const int vx = P.lay_vox[j];
+      const float val = g[j] * P.inv3c2[j];
+      Q.rho[0][vx] = val;
+      Q.rho[1][vx] = val;
+      Q.rho[2][vx] = val;
+      zf[loc(P.lay_pf[j])] = P.c2[vx] * (3.f * val);
+    }
+  }
+  __syncthreads();
+  if (role == ROLE_FORWARD) {
+    float* f = P.traces + ((size_t)shot * P.nt + tix) * P.n_rec;
+    for (int e = P.rr_ptr[key0] + threadIdx.x; e < P.rr_ptr[key1]; e += G::NT) f[P.rr_col[e]] = zf[loc(P.rr_pf[e])];
+    if (P.record_layer) {
+      float* g = P.ghist + ((size_t)shot * P.nt + tix) * P.n_layer;
+      for (int j = P.lay_ptr[key0] + threadIdx.x; j < P.lay_ptr[key1]; j += G::NT) g[j] = zf[loc(P.lay_pf[j])];
+    }
+  } else {
+    float* out = role == ROLE_ADJOINT ? P.pa + (size_t)shot * P.n_gamma
+                                      : P.ring + ((size_t)shot * 3 + P.slot[blockIdx.z]) * P.n_gamma;
+    for (int j = P.gam_ptr[key0] + threadIdx.x; j < P.gam_ptr[key1]; j += G::NT) out[j] = zf[loc(P.gam_pf[j])];
+  }
+  __syncthreads();
+  // forward x step A of p (pairs in X) -> S, then step B, R2C unpacking -> rows of spec[0]
+  for (int t = threadIdx.x; t < G::T4; t += G::NT) {
+    const int p = t / G::AX1, k1 = t - p * G::AX1;
+    if (2 * p >= nyl) continue;
+    const float2* r = X + p * G::PST + k1;
+    float2 zz[G::AX2];
+    sfor<0, G::AX2>([&](auto K2) { zz[decltype(K2)::value] = r[G::AX1 * decltype(K2)::value]; });
+    p2_xfwd_a<G>(zz, p, k1, S, twxT);
+  }
+  __syncthreads();
+  p2_xfwd_b<G>(S, X);
+  __syncthreads();
+  x2_unpack_store<G>(X, Q.spec[0] + soff, p0, ny);
+}
+
+}  // namespace fwi

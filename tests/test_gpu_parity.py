@@ -223,3 +223,23 @@ def test_two_step_plane_kernels_gradient_parity(shape, pairing):
         assert oc.rel(traces[k].cpu().numpy(), f_ref[k]) < TOL_TRACES
     assert np.all(np.abs(D.cpu().numpy() - D_ref) <= TOL_MISFIT * np.abs(D_ref))
     assert oc.rel(g.cpu().numpy().reshape(wl.shape), g_ref) < TOL_GRAD
+
+
+@pytest.mark.parametrize("shape,pairing", [((243, 243, 8), "literal"), ((256, 256, 6), "exact")])
+def test_two_step_split_plane_gradient_parity(shape, pairing):
+    """The two-step split-plane kernels (column passes and row-pair passes through global
+    memory, schedule specialized = 2 with split planes) against the oracle gradient."""
+    from paper_2102_00755_b300 import autotune
+    wl = synth.small_workload(*shape, 90, pml=3, n_src=3, n_rec=20, K=2, layer=2, seed=12,
+                              f0=0.5e6, gamma_frac=0.3)
+    f_obs = oc.observed(wl)
+    f_ref, D_ref, g_ref = oc.gradient(wl, f_obs, pairing, c_rec=wl.c_rec)
+    plan = fwi.Plan.from_workload(wl, pairing=pairing, max_shots=len(wl.weights))
+    assert autotune.set_schedule(plan, dict(specialized=2, radix_order=0, z_tile=16, split_plane=1)) == fwi.FWI_OK
+    traces = torch.empty((len(wl.weights), wl.nt, len(wl.rec_idx)), dtype=torch.float32, device="cuda")
+    D, g = plan.gradient(dev(wl.c_model), dev(wl.weights), dev(f_obs), traces=traces)
+    assert plan.status() == fwi.FWI_OK
+    for k in range(len(wl.weights)):
+        assert oc.rel(traces[k].cpu().numpy(), f_ref[k]) < TOL_TRACES
+    assert np.all(np.abs(D.cpu().numpy() - D_ref) <= TOL_MISFIT * np.abs(D_ref))
+    assert oc.rel(g.cpu().numpy().reshape(wl.shape), g_ref) < TOL_GRAD
