@@ -15,7 +15,9 @@ nothing else is borrowed):
   Dirichlet boundary layer, and the interleaved adjoint/TR loop assembling the
   gradient 2/(dt c0^3) (p+ - 2 p0 + p-) p_adj on Gamma: Alg. 1, second part
   (continuous counterpart Eq. 10 and TR wave equation Eq. 11, Sec. 3.1).
-* source encoding: s_hat = sum_i w_i s_i, f_hat = sum_i w_i f_i (Sec. 3.2).
+* source encoding: s_hat = sum_i w_i s_i, f_hat = sum_i w_i f_i (Sec. 3.2), and the
+  delayed encoding of Eq. 13: s_hat(t) = sum_i w_i s_i(t - d_i tau), f_hat(t) =
+  sum_i w_i f_i(t - d_i tau), with each delay d_i tau a whole number of time steps.
 
 Readings where the paper is silent (all listed in the design notes):
 * sinc is the unnormalised sin(x)/x, sinc(0) = 1; c_ref = c_max fixes both
@@ -165,8 +167,9 @@ def injection_map(G: Grid, c: np.ndarray, idx: np.ndarray, amp: np.ndarray) -> n
 
 
 def forward(G: Grid, c: np.ndarray, src_idx, src_weights, wavelet, rec_idx, layer_idx=None,
-            nt=None, gamma_idx=None, record_field=False):
-    """Forward iteration of Alg. 1 for the encoded source sum_i w_i s_i.
+            nt=None, gamma_idx=None, record_field=False, delays=None):
+    """Forward iteration of Alg. 1 for the encoded source sum_i w_i s_i, or, with
+    delays (whole time steps per source, Eq. 13), sum_i w_i s(t_n - delays_i dt).
 
     Returns f [nt, n_rec], g [nt, n_layer] (or None), and, if gamma_idx is given,
     the stored forward field on Gamma [nt, n_gamma] (the 'full' variant);
@@ -182,8 +185,16 @@ def forward(G: Grid, c: np.ndarray, src_idx, src_weights, wavelet, rec_idx, laye
     w = np.asarray(src_weights, dtype=np.float64)
     src_idx = np.asarray(src_idx)
     base = injection_map(G, c, src_idx, w)            # time-independent part of S s_hat
+    if delays is not None:
+        delays = np.asarray(delays, dtype=np.int64)
     for n in range(nt):
-        step(G, S, c2, mass_src=base * wavelet[n])
+        if delays is None:
+            src = base * wavelet[n]
+        else:                                          # source i emits s(t_n - delays_i dt)
+            m = n - delays
+            s_i = np.where((m >= 0) & (m < len(wavelet)), np.asarray(wavelet)[np.clip(m, 0, len(wavelet) - 1)], 0.0)
+            src = injection_map(G, c, src_idx, w * s_i)
+        step(G, S, c2, mass_src=src)
         pf = S.p.reshape(-1)
         f[n] = pf[rec_idx]                            # f^n = M p
         if g is not None:
@@ -200,9 +211,20 @@ def forward(G: Grid, c: np.ndarray, src_idx, src_weights, wavelet, rec_idx, laye
     return tuple(out)
 
 
-def encode_data(weights, data):
-    """f_hat = sum_i w_i f_i for per-source data [n_src, nt, n_rec] (Sec. 3.2)."""
-    return np.tensordot(np.asarray(weights, dtype=np.float64), np.asarray(data, dtype=np.float64), axes=1)
+def encode_data(weights, data, delays=None, nt=None):
+    """f_hat = sum_i w_i f_i for per-source data [n_src, nt_data, n_rec] (Sec. 3.2); with
+    delays (whole time steps), f_hat[n] = sum_i w_i f_i[n - delays_i] (Eq. 13), zero
+    where n - delays_i falls outside the data, over nt samples (default nt_data)."""
+    w = np.asarray(weights, dtype=np.float64)
+    data = np.asarray(data, dtype=np.float64)
+    if delays is None:
+        return np.tensordot(w, data, axes=1)
+    nt = data.shape[1] if nt is None else nt
+    out = np.zeros((nt, data.shape[2]))
+    for i, d in enumerate(np.asarray(delays, dtype=np.int64)):
+        for n in range(max(0, d), min(nt, d + data.shape[1])):
+            out[n] += w[i] * data[i, n - d]
+    return out
 
 
 def adjoint_source(f, f_obs):
@@ -286,13 +308,15 @@ def gradient(G: Grid, c: np.ndarray, f, f_obs, rec_idx, layer_idx, gamma_idx, g,
 
 
 def fwi_gradient(G: Grid, c, src_idx, weights, wavelet, rec_idx, layer_idx, gamma_idx, f_obs,
-                 pairing="literal", c_rec=None, full=False):
-    """Forward + gradient for one encoded super-shot (weights [n_src])."""
+                 pairing="literal", c_rec=None, full=False, delays=None):
+    """Forward + gradient for one encoded super-shot (weights [n_src]; delays [n_src] in
+    time steps for the delayed encoding of Eq. 13, f_obs then encoded with the same delays)."""
     if full:
-        f, g, hist = forward(G, c, src_idx, weights, wavelet, rec_idx, layer_idx, gamma_idx=gamma_idx)
+        f, g, hist = forward(G, c, src_idx, weights, wavelet, rec_idx, layer_idx, gamma_idx=gamma_idx,
+                             delays=delays)
         return (f,) + gradient(G, c, f, f_obs, rec_idx, layer_idx, gamma_idx, g, pairing,
                                history=hist, c_rec=c_rec)
-    f, g = forward(G, c, src_idx, weights, wavelet, rec_idx, layer_idx)
+    f, g = forward(G, c, src_idx, weights, wavelet, rec_idx, layer_idx, delays=delays)
     return (f,) + gradient(G, c, f, f_obs, rec_idx, layer_idx, gamma_idx, g, pairing, c_rec=c_rec)
 
 

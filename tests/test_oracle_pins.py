@@ -452,3 +452,65 @@ def test_closed_form_traces_match_time_stepping(shape, c):
     cf = closed_form.homogeneous_traces(shape, G.dx, G.dt, C_REF, c, src, rec, s, nt)
     assert np.abs(f).max() > 0
     assert np.abs(cf - f).max() < 1e-11 * np.abs(f).max()
+
+
+# ---------------------------------------------------------------------------
+# Delayed source encoding (Eq. 13, App. D): whole-step delays
+# ---------------------------------------------------------------------------
+def _delay_setup():
+    G = _grid(12, 10, 9)
+    nt = 50
+    rng = np.random.default_rng(8)
+    c = 1500.0 + 40.0 * rng.random(G.shape)
+    src = np.array([5 + 12 * (4 + 10 * 4), 2 + 12 * (7 + 10 * 2), 9 + 12 * (1 + 10 * 6)])
+    rec = rng.choice(12 * 10 * 9, size=6, replace=False)
+    s = synth.ricker(nt, G.dt, 0.4e6)
+    return G, nt, c, src, rec, s
+
+
+def test_delayed_source_emits_later():
+    """One source delayed by d steps: s(t - d dt) gives the undelayed traces d samples later,
+    and exact zeros before (the field starts from rest)."""
+    G, nt, c, src, rec, s = _delay_setup()
+    f0, _ = pstd.forward(G, c, src[:1], [1.0], s, rec)
+    f7, _ = pstd.forward(G, c, src[:1], [1.0], s, rec, delays=[7])
+    assert np.all(f7[:7] == 0.0)
+    assert np.abs(f0).max() > 0
+    assert np.abs(f7[7:] - f0[:-7]).max() < 1e-12 * np.abs(f0).max()
+
+
+def test_delayed_encoding_is_shifted_superposition():
+    """p_hat(t) = sum_i w_i p_i(t - d_i tau) by linearity and time invariance (App. D)."""
+    G, nt, c, src, rec, s = _delay_setup()
+    w = np.array([1.0, -1.0, 1.0])
+    d = np.array([0, 5, 11])
+    f_hat, _ = pstd.forward(G, c, src, w, s, rec, delays=d)
+    ref = np.zeros_like(f_hat)
+    for i in range(3):
+        fi, _ = pstd.forward(G, c, src[i:i + 1], [1.0], s, rec)
+        ref[d[i]:] += w[i] * fi[:nt - d[i]]
+    assert np.abs(f_hat - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_zero_delays_are_conventional_encoding():
+    G, nt, c, src, rec, s = _delay_setup()
+    w = np.array([1.0, -1.0, -1.0])
+    fa, _ = pstd.forward(G, c, src, w, s, rec)
+    fb, _ = pstd.forward(G, c, src, w, s, rec, delays=[0, 0, 0])
+    assert np.abs(fa - fb).max() < 1e-13 * np.abs(fa).max()
+
+
+def test_delayed_data_encoding_closed_form():
+    """data_i[n][r] = (i + 1)(n + 1) + r: f_hat[n][r] = sum over sources with
+    0 <= n - d_i < nt_data of w_i ((i + 1)(n - d_i + 1) + r)."""
+    n_src, nt_d, n_rec, nt = 3, 6, 2, 10
+    data = np.array([[[(i + 1) * (n + 1) + r for r in range(n_rec)] for n in range(nt_d)] for i in range(n_src)],
+                    dtype=float)
+    w, d = [1.0, -1.0, 1.0], [0, 2, 5]
+    out = pstd.encode_data(w, data, delays=d, nt=nt)
+    assert out.shape == (nt, n_rec)
+    # n = 7: source 0 has ended (7 >= 6), source 1 at 5: -(2*6 + r), source 2 at 2: 3*3 + r
+    assert list(out[7]) == [-12.0 + 9.0, -13.0 + 10.0]
+    # n = 0: only source 0: 1*1 + r
+    assert list(out[0]) == [1.0, 2.0]
+    assert np.allclose(pstd.encode_data(w, data), pstd.encode_data(w, data, delays=[0, 0, 0]))
