@@ -137,6 +137,28 @@ fwi_status fwi_gradient(fwi_plan *plan, const float *c, const float *weights, in
                         double *grad, float *traces, void *stream);
 
 /*
+ * Delayed source encoding (Sec. 3.2, Eq. 13): emitter i of super-shot k fires the
+ * plan's wavelet delayed by delay[k][i] time steps, s_hat(t_n) = sum_i w_ki
+ * s(t_n - delay_ki dt), and the observed data are encoded with the same delays,
+ * f_hat[n] = sum_i w_ki f_i[n - delay_ki].  The random delays d_i tau of Eq. 13 are
+ * given as whole time steps (0 <= delay < nt); the plan's nt must cover the data
+ * length plus the largest delay (T + tau), and its wavelet is the undelayed pulse
+ * (zero-padded to nt).  Delays outside [0, nt) simply emit nothing in the window.
+ *   delay:       device [K][n_src] int32
+ *   observed:    observed_encoded = 1: [K][nt][n_rec] already delay-encoded;
+ *                observed_encoded = 0: raw per-source data [n_src][observed_nt][n_rec],
+ *                1 <= observed_nt <= nt, zero beyond its samples
+ * Other arguments, outputs and errors as for fwi_forward / fwi_gradient.  All delays
+ * zero give exactly the results of fwi_forward / fwi_gradient.
+ */
+fwi_status fwi_forward_delayed(fwi_plan *plan, const float *c, const float *weights,
+                               const int32_t *delay, int32_t K, float *traces, void *stream);
+fwi_status fwi_gradient_delayed(fwi_plan *plan, const float *c, const float *weights,
+                                const int32_t *delay, int32_t K, const float *observed,
+                                int32_t observed_encoded, int32_t observed_nt, double *misfit,
+                                double *grad, float *traces, void *stream);
+
+/*
  * Wait for the plan's last call and report its device-side status:
  * FWI_EUNSTABLE if its sound speed was outside (0, c_ref] (the call's outputs are
  * then undefined), FWI_ECUDA on an asynchronous CUDA error, else FWI_OK.

@@ -60,16 +60,26 @@ __global__ void k_prepare_coefs(const float* __restrict__ c, double dt, double d
 }
 
 // amp[k][n][u] = coef_u * (sum_{i at u} w[k][i]) * s(t_n): the encoded source (Sec. 3.2)
+// delay (optional, [K][n_src] whole time steps, Eq. 13): emitter i of super-shot k
+// emits s(t_n - delay dt), zero outside the wavelet's samples
 __global__ void k_source_amp(const float* __restrict__ w, int n_src, const float* __restrict__ coef,
                              const int* mptr, const int* mem, int n_us, const float* __restrict__ wav,
-                             int nt, float* __restrict__ amp) {
+                             int nt, const int* __restrict__ delay, float* __restrict__ amp) {
   const int n = blockIdx.x;
   const int k = blockIdx.y;
   const float s = wav[n];
   for (int u = threadIdx.x; u < n_us; u += blockDim.x) {
     float ws = 0.f;
-    for (int e = mptr[u]; e < mptr[u + 1]; ++e) ws += w[(size_t)k * n_src + mem[e]];
-    amp[((size_t)k * nt + n) * n_us + u] = coef[u] * ws * s;
+    for (int e = mptr[u]; e < mptr[u + 1]; ++e) {
+      const size_t ki = (size_t)k * n_src + mem[e];
+      if (delay) {
+        const int m = n - delay[ki];
+        if (m >= 0 && m < nt) ws += w[ki] * wav[m];
+      } else {
+        ws += w[ki];
+      }
+    }
+    amp[((size_t)k * nt + n) * n_us + u] = coef[u] * (delay ? ws : ws * s);
   }
 }
 
@@ -85,6 +95,27 @@ __global__ void k_encode(const float* __restrict__ raw, const float* __restrict_
       for (int k = 0; k < K; ++k) acc[k] += (double)w[(size_t)k * n_src + i] * v;
     }
     for (int k = 0; k < K; ++k) out[(size_t)k * per_src + e] = (float)acc[k];
+  }
+}
+
+// f_hat[k][n][r] = sum_i w[k][i] f_i[n - d[k][i]][r] (Eq. 13, whole-step delays), zero
+// where n - d falls outside the nt_obs recorded samples; FP64 accumulation
+__global__ void k_encode_delayed(const float* __restrict__ raw, const float* __restrict__ w,
+                                 const int* __restrict__ delay, int n_src, int K, int nt_obs, int nt,
+                                 int n_rec, float* __restrict__ out) {
+  const int64_t tot = (int64_t)nt * n_rec;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(e / n_rec), r = (int)(e - (int64_t)n * n_rec);
+    double acc[kMaxSims];
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (int i = 0; i < n_src; ++i) {
+      for (int k = 0; k < K; ++k) {
+        const int m = n - delay[(size_t)k * n_src + i];
+        if (m >= 0 && m < nt_obs)
+          acc[k] += (double)w[(size_t)k * n_src + i] * (double)raw[((size_t)i * nt_obs + m) * n_rec + r];
+      }
+    }
+    for (int k = 0; k < K; ++k) out[(size_t)k * tot + e] = (float)acc[k];
   }
 }
 
@@ -776,12 +807,12 @@ fwi_status prepare(fwi_plan* p, const float* c, cudaStream_t st) {
   return FWI_OK;
 }
 
-fwi_status run_forward(fwi_plan* p, const float* w, int K, bool record_layer, float* traces,
-                       cudaStream_t st) {
+fwi_status run_forward(fwi_plan* p, const float* w, const int* delay, int K, bool record_layer,
+                       float* traces, cudaStream_t st) {
   const fwi_problem& q = p->prob;
   k_source_amp<<<dim3(q.nt, K), 128, 0, st>>>(w, q.n_src, at<float>(p, p->o_us_coef),
                                               at<int>(p, p->o_us_mptr), at<int>(p, p->o_us_mem), p->n_us,
-                                              at<float>(p, p->o_wav), q.nt, at<float>(p, p->o_amp));
+                                              at<float>(p, p->o_wav), q.nt, delay, at<float>(p, p->o_amp));
   LAUNCHED("k_source_amp");
   StepParams P;
   base_params(p, &P);
@@ -1028,8 +1059,9 @@ fwi_status fwi_plan_bind_workspace(fwi_plan* p, void* dev_ptr, size_t bytes) {
   return FWI_OK;
 }
 
-fwi_status fwi_forward(fwi_plan* p, const float* c, const float* weights, int32_t K, float* traces,
-                       void* stream) {
+namespace {
+fwi_status forward_impl(fwi_plan* p, const float* c, const float* weights, const int* delay, int32_t K,
+                        float* traces, void* stream) {
   fwi_status s = check_call(p, K);
   if (s != FWI_OK) return s;
   if (!c || !weights || !traces) return FWI_EINVAL;
@@ -1037,12 +1069,43 @@ fwi_status fwi_forward(fwi_plan* p, const float* c, const float* weights, int32_
   p->last = st;
   p->used = true;
   if ((s = prepare(p, c, st)) != FWI_OK) return s;
-  return run_forward(p, weights, K, false, traces, st);
+  return run_forward(p, weights, delay, K, false, traces, st);
 }
+fwi_status gradient_impl(fwi_plan* p, const float* c, const float* weights, const int* delay, int32_t K,
+                         const float* observed, int32_t observed_encoded, int32_t observed_nt, double* misfit,
+                         double* grad, float* traces, void* stream);
+}  // namespace
 
+fwi_status fwi_forward(fwi_plan* p, const float* c, const float* weights, int32_t K, float* traces,
+                       void* stream) {
+  return forward_impl(p, c, weights, nullptr, K, traces, stream);
+}
+fwi_status fwi_forward_delayed(fwi_plan* p, const float* c, const float* weights, const int32_t* delay,
+                               int32_t K, float* traces, void* stream) {
+  if (!delay) return FWI_EINVAL;
+  return forward_impl(p, c, weights, delay, K, traces, stream);
+}
 fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32_t K,
                         const float* observed, int32_t observed_encoded, double* misfit, double* grad,
                         float* traces, void* stream) {
+  return gradient_impl(p, c, weights, nullptr, K, observed, observed_encoded, p ? p->prob.nt : 0, misfit,
+                       grad, traces, stream);
+}
+fwi_status fwi_gradient_delayed(fwi_plan* p, const float* c, const float* weights, const int32_t* delay,
+                                int32_t K, const float* observed, int32_t observed_encoded,
+                                int32_t observed_nt, double* misfit, double* grad, float* traces,
+                                void* stream) {
+  if (!delay || !p) return FWI_EINVAL;
+  if (!observed_encoded && (observed_nt < 1 || observed_nt > p->prob.nt)) return FWI_EINVAL;
+  return gradient_impl(p, c, weights, delay, K, observed, observed_encoded, observed_nt, misfit, grad, traces,
+                       stream);
+}
+
+namespace {
+
+fwi_status gradient_impl(fwi_plan* p, const float* c, const float* weights, const int* delay, int32_t K,
+                         const float* observed, int32_t observed_encoded, int32_t observed_nt, double* misfit,
+                         double* grad, float* traces, void* stream) {
   fwi_status s = check_call(p, K);
   if (s != FWI_OK) return s;
   if (!c || !weights || !observed || !misfit || !grad) return FWI_EINVAL;
@@ -1055,13 +1118,19 @@ fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32
   // observed data, encoded
   const float* obs = observed;
   if (!observed_encoded) {
-    const int64_t per = (int64_t)nt * q.n_rec;
-    k_encode<<<592, 256, 0, st>>>(observed, weights, q.n_src, K, per, at<float>(p, p->o_obs));
-    LAUNCHED("k_encode");
+    if (delay) {
+      k_encode_delayed<<<592, 256, 0, st>>>(observed, weights, delay, q.n_src, K, observed_nt, nt, q.n_rec,
+                                            at<float>(p, p->o_obs));
+      LAUNCHED("k_encode_delayed");
+    } else {
+      const int64_t per = (int64_t)nt * q.n_rec;
+      k_encode<<<592, 256, 0, st>>>(observed, weights, q.n_src, K, per, at<float>(p, p->o_obs));
+      LAUNCHED("k_encode");
+    }
     obs = at<float>(p, p->o_obs);
   }
   // forward, recording traces and the boundary-layer history
-  if ((s = run_forward(p, weights, K, true, at<float>(p, p->o_traces), st)) != FWI_OK) return s;
+  if ((s = run_forward(p, weights, delay, K, true, at<float>(p, p->o_traces), st)) != FWI_OK) return s;
   // residual, misfit, cumulative sum
   k_misfit<<<dim3(p->nblk_misfit, K), 256, 0, st>>>(at<float>(p, p->o_traces), obs, nt, q.n_rec,
                                                     at<float>(p, p->o_qf), at<double>(p, p->o_dpart));
@@ -1146,6 +1215,7 @@ fwi_status fwi_gradient(fwi_plan* p, const float* c, const float* weights, int32
   CK(cudaGetLastError());
   return FWI_OK;
 }
+}  // namespace
 
 fwi_status fwi_plan_status(fwi_plan* p) {
   if (!p || !p->ws) return FWI_EINVAL;

@@ -29,6 +29,7 @@ FWI_ENOTSUP = 7
 PAIRING = {"literal": 0, "exact": 1}
 
 C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_gradient",
+             "fwi_forward_delayed", "fwi_gradient_delayed",
              "fwi_plan_status", "fwi_plan_voxel_steps", "fwi_plan_launches", "fwi_plan_profile",
              "fwi_plan_profile_read", "fwi_plan_set_schedule", "fwi_plan_get_schedule",
              "fwi_adjoint_source_noalloc", "fwi_batch_create",
@@ -89,6 +90,10 @@ def lib():
         L.fwi_forward.restype = ctypes.c_int
         L.fwi_gradient.argtypes = [vp, vp, vp, i32, vp, i32, vp, vp, vp, vp]
         L.fwi_gradient.restype = ctypes.c_int
+        L.fwi_forward_delayed.argtypes = [vp, vp, vp, vp, i32, vp, vp]
+        L.fwi_forward_delayed.restype = ctypes.c_int
+        L.fwi_gradient_delayed.argtypes = [vp, vp, vp, vp, i32, vp, i32, i32, vp, vp, vp, vp]
+        L.fwi_gradient_delayed.restype = ctypes.c_int
         L.fwi_plan_status.argtypes = [vp]
         L.fwi_plan_status.restype = ctypes.c_int
         L.fwi_plan_voxel_steps.argtypes = [vp, i32, i32]
@@ -150,6 +155,16 @@ def fwi_gradient(plan, c_ptr, w_ptr, K, obs_ptr, obs_encoded, misfit_ptr, grad_p
                  stream) -> int:
     return lib().fwi_gradient(plan, c_ptr, w_ptr, K, obs_ptr, obs_encoded, misfit_ptr, grad_ptr,
                               traces_ptr, stream)
+
+
+def fwi_forward_delayed(plan, c_ptr, w_ptr, d_ptr, K, traces_ptr, stream) -> int:
+    return lib().fwi_forward_delayed(plan, c_ptr, w_ptr, d_ptr, K, traces_ptr, stream)
+
+
+def fwi_gradient_delayed(plan, c_ptr, w_ptr, d_ptr, K, obs_ptr, obs_encoded, obs_nt, misfit_ptr, grad_ptr,
+                         traces_ptr, stream) -> int:
+    return lib().fwi_gradient_delayed(plan, c_ptr, w_ptr, d_ptr, K, obs_ptr, obs_encoded, obs_nt, misfit_ptr,
+                                      grad_ptr, traces_ptr, stream)
 
 
 def fwi_plan_status(plan) -> int:
@@ -300,29 +315,49 @@ class Plan:
         return self.nx * self.ny * self.nz
 
     def forward(self, c: torch.Tensor, weights: torch.Tensor, traces: torch.Tensor = None,
-                stream=None) -> torch.Tensor:
+                stream=None, delays: torch.Tensor = None) -> torch.Tensor:
+        """Forward traces; `delays` (int32 [K][n_src], time steps) selects the delayed
+        source encoding (fwi_forward_delayed)."""
         K = weights.shape[0]
         if traces is None:
             traces = torch.empty((K, self.nt, self.n_rec), dtype=torch.float32, device=c.device)
-        st = fwi_forward(self.handle, _dptr(c, torch.float32, "c"), _dptr(weights, torch.float32, "weights"),
-                         K, _dptr(traces, torch.float32, "traces"), _stream_handle(stream))
-        _check(st, "fwi_forward")
+        if delays is None:
+            st = fwi_forward(self.handle, _dptr(c, torch.float32, "c"), _dptr(weights, torch.float32, "weights"),
+                             K, _dptr(traces, torch.float32, "traces"), _stream_handle(stream))
+            _check(st, "fwi_forward")
+        else:
+            st = fwi_forward_delayed(self.handle, _dptr(c, torch.float32, "c"),
+                                     _dptr(weights, torch.float32, "weights"), _dptr(delays, torch.int32, "delays"),
+                                     K, _dptr(traces, torch.float32, "traces"), _stream_handle(stream))
+            _check(st, "fwi_forward_delayed")
         return traces
 
     def gradient(self, c: torch.Tensor, weights: torch.Tensor, observed: torch.Tensor, encoded=True,
-                 misfit=None, grad=None, traces=None, stream=None):
+                 misfit=None, grad=None, traces=None, stream=None, delays: torch.Tensor = None):
+        """Misfit and gradient; with `delays` (int32 [K][n_src]) the delayed source encoding
+        (fwi_gradient_delayed; raw observed data may be shorter than nt)."""
         K = weights.shape[0]
         if misfit is None:
             misfit = torch.empty(K, dtype=torch.float64, device=c.device)
         if grad is None:
             grad = torch.empty(self.n_vox, dtype=torch.float64, device=c.device)
         tp = _dptr(traces, torch.float32, "traces") if traces is not None else ctypes.c_void_p(0)
-        st = fwi_gradient(self.handle, _dptr(c, torch.float32, "c"),
-                          _dptr(weights, torch.float32, "weights"), K,
-                          _dptr(observed, torch.float32, "observed"), 1 if encoded else 0,
-                          _dptr(misfit, torch.float64, "misfit"), _dptr(grad, torch.float64, "grad"),
-                          tp, _stream_handle(stream))
-        _check(st, "fwi_gradient")
+        if delays is None:
+            st = fwi_gradient(self.handle, _dptr(c, torch.float32, "c"),
+                              _dptr(weights, torch.float32, "weights"), K,
+                              _dptr(observed, torch.float32, "observed"), 1 if encoded else 0,
+                              _dptr(misfit, torch.float64, "misfit"), _dptr(grad, torch.float64, "grad"),
+                              tp, _stream_handle(stream))
+            _check(st, "fwi_gradient")
+        else:
+            obs_nt = observed.shape[1] if observed.dim() == 3 else self.nt
+            st = fwi_gradient_delayed(self.handle, _dptr(c, torch.float32, "c"),
+                                      _dptr(weights, torch.float32, "weights"),
+                                      _dptr(delays, torch.int32, "delays"), K,
+                                      _dptr(observed, torch.float32, "observed"), 1 if encoded else 0, obs_nt,
+                                      _dptr(misfit, torch.float64, "misfit"), _dptr(grad, torch.float64, "grad"),
+                                      tp, _stream_handle(stream))
+            _check(st, "fwi_gradient_delayed")
         return misfit, grad
 
     def status(self) -> int:

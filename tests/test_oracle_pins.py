@@ -514,3 +514,80 @@ def test_delayed_data_encoding_closed_form():
     # n = 0: only source 0: 1*1 + r
     assert list(out[0]) == [1.0, 2.0]
     assert np.allclose(pstd.encode_data(w, data), pstd.encode_data(w, data, delays=[0, 0, 0]))
+
+
+# ---------------------------------------------------------------------------
+# Stochastic L-BFGS (Alg. 2)
+# ---------------------------------------------------------------------------
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return Q @ np.diag(np.linspace(1.0, 20.0, n)) @ Q.T, rng.standard_normal(n)
+
+
+def test_two_loop_secant_condition():
+    """Secant condition of the BFGS update: after each new pair (s, y), H y = s for that
+    pair, whatever the earlier pairs and the initial scaling."""
+    from oracle import slbfgs
+    A, _ = _spd(8, 1)
+    rng = np.random.default_rng(2)
+    S, Y = [], []
+    for k in range(8):
+        s = rng.standard_normal(8)
+        assert slbfgs.push_pair(S, Y, s, A @ s, 64)
+        h = slbfgs.two_loop(Y[-1], S, Y, 0.7)
+        assert np.allclose(h, S[-1], rtol=1e-10, atol=1e-12)
+
+
+def test_two_loop_equals_dense_bfgs_update():
+    """The two-loop recursion equals the dense BFGS inverse update
+    H+ = (I - rho s y') H (I - rho y s') + rho s s' applied pair by pair from h0 I."""
+    from oracle import slbfgs
+    A, g = _spd(6, 3)
+    rng = np.random.default_rng(4)
+    S, Y = [], []
+    H = 0.3 * np.eye(6)
+    for _ in range(4):
+        s = rng.standard_normal(6)
+        y = A @ s
+        slbfgs.push_pair(S, Y, s, y, 64)
+        rho = 1.0 / (y @ s)
+        V = np.eye(6) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    assert np.allclose(slbfgs.two_loop(g, S, Y, 0.3), H @ g, rtol=1e-10, atol=1e-12)
+
+
+def test_history_limit_and_curvature_skip():
+    from oracle import slbfgs
+    S, Y = [], []
+    for k in range(5):
+        slbfgs.push_pair(S, Y, np.array([1.0, k]), np.array([1.0, 0.5]), 3)
+    assert len(S) == 3 and S[0][1] == 2.0
+    assert not slbfgs.push_pair(S, Y, np.array([1.0, 0.0]), np.array([-1.0, 0.0]), 3)
+    assert len(S) == 3
+
+
+def test_slbfgs_exact_gradients_reach_quadratic_minimum():
+    """theta = 0 (exact energy and gradient): the iterates converge to A^-1 b."""
+    from oracle import slbfgs
+    A, b = _spd(10, 5)
+    est = lambda u, th, n: (0.5 * u @ A @ u - b @ u, A @ u - b)
+    u_hat, Js, _ = slbfgs.slbfgs(np.zeros(10), est, nu=1.0, n_evl=60, m=64)
+    assert np.linalg.norm(u_hat - np.linalg.solve(A, b)) < 1e-8 * np.linalg.norm(np.linalg.solve(A, b))
+
+
+def test_slbfgs_projection_and_averaging():
+    """Bounds are enforced after every step, and after the first energy increase the
+    returned estimate is the w(i) = i^3 weighted mean of the later iterates."""
+    from oracle import slbfgs
+    rng = np.random.default_rng(6)
+    A, b = _spd(5, 7)
+    def est(u, th, n):               # noisy gradient, same noise for the same n
+        e = np.random.default_rng(n).standard_normal(5)
+        return 0.5 * u @ A @ u - b @ u + 0.1 * (e @ u), A @ u - b + 0.1 * e
+    u_hat, Js, us = slbfgs.slbfgs(rng.standard_normal(5), est, nu=0.5, n_evl=40, m=8, u_min=-0.2, u_max=0.2)
+    assert all(np.all(u >= -0.2) and np.all(u <= 0.2) for u in us)
+    first = next(i for i in range(1, len(Js)) if Js[i] > Js[i - 1])     # 0-based iteration index
+    idx = range(first + 1, len(us))
+    w = np.array([(i + 1) ** 3 for i in idx], dtype=float)
+    assert np.allclose(u_hat, sum(wi * us[i] for wi, i in zip(w, idx)) / w.sum())
