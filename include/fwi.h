@@ -159,6 +159,51 @@ fwi_status fwi_gradient_delayed(fwi_plan *plan, const float *c, const float *wei
                                 double *grad, float *traces, void *stream);
 
 /*
+ * Stochastic L-BFGS (Alg. 2) on the device: an L-BFGS history of at most m pairs
+ * (s, y) of n-vectors, stored in FP32 in a caller-owned workspace, with every dot
+ * product accumulated in FP64.  Alg. 2 evaluates the gradient estimator twice per
+ * iteration with the same stochastic approximation and stores the pair
+ * (nu z, G_z - G_u); the two-loop recursion gives the step z = -H G.
+ *   fwi_lbfgs_create:  sizes the workspace (2 m n floats + small scratch).
+ *   fwi_lbfgs_bind_workspace: caller-owned device memory, 256-byte aligned; empties
+ *                      the history.
+ *   fwi_lbfgs_push:    adds the pair (s, y) (device FP64 [n] each) unless s'y <= 0
+ *                      (the pair is then skipped, *stored = 0), dropping the oldest
+ *                      pair beyond m.  Synchronous on `stream` (it reads s'y and y'y).
+ *   fwi_lbfgs_apply:   out = H g (device FP64 [n]; out may equal g), H_0 = h0 I, or
+ *                      (s'y / y'y) I of the newest pair if h0 <= 0 (I if empty).
+ *                      Asynchronous.
+ *   fwi_lbfgs_size:    number of stored pairs.
+ * Errors: FWI_EINVAL (NULL, n <= 0, m outside 1..1024, unbound or misaligned
+ * workspace), FWI_ECUDA.
+ */
+typedef struct fwi_lbfgs fwi_lbfgs;
+fwi_status fwi_lbfgs_create(int64_t n, int32_t m, size_t *workspace_bytes, fwi_lbfgs **out);
+fwi_status fwi_lbfgs_bind_workspace(fwi_lbfgs *lbfgs, void *dev_ptr, size_t bytes);
+fwi_status fwi_lbfgs_push(fwi_lbfgs *lbfgs, const double *s, const double *y, void *stream,
+                          int32_t *stored);
+fwi_status fwi_lbfgs_apply(fwi_lbfgs *lbfgs, const double *g, double h0, double *out, void *stream);
+int32_t fwi_lbfgs_size(const fwi_lbfgs *lbfgs);
+fwi_status fwi_lbfgs_destroy(fwi_lbfgs *lbfgs);
+
+/*
+ * Elementwise steps of Alg. 2 and of the parameterisations of Sec. 3.3, on device
+ * vectors of length n (asynchronous on `stream`):
+ *   fwi_vec_step_project: u <- min(max(u + nu z, u_min), u_max)   (projection step)
+ *   fwi_vec_accumulate:   acc <- acc + w u                         (iterate averaging)
+ *   fwi_param_to_speed:   c <- c(u) for u = c (kind 0), u = 1/c (1, slowness),
+ *                         u = 1/c^2 (2, squared slowness)
+ *   fwi_grad_to_param:    g_u <- g_c dc/du: 1, -c^2, -c^3 / 2 for kinds 0, 1, 2
+ * Errors: FWI_EINVAL (NULL, n <= 0, bad kind, u_min > u_max), FWI_ECUDA.
+ */
+fwi_status fwi_vec_step_project(int64_t n, double *u, const double *z, double nu, double u_min,
+                                double u_max, void *stream);
+fwi_status fwi_vec_accumulate(int64_t n, double *acc, const double *u, double w, void *stream);
+fwi_status fwi_param_to_speed(int64_t n, int32_t kind, const double *u, float *c, void *stream);
+fwi_status fwi_grad_to_param(int64_t n, int32_t kind, const float *c, const double *gc, double *gu,
+                             void *stream);
+
+/*
  * Wait for the plan's last call and report its device-side status:
  * FWI_EUNSTABLE if its sound speed was outside (0, c_ref] (the call's outputs are
  * then undefined), FWI_ECUDA on an asynchronous CUDA error, else FWI_OK.

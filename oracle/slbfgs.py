@@ -17,6 +17,10 @@ Readings where Alg. 2 leaves a choice:
 * A pair with s'y <= 0 (no positive curvature) is not stored, which keeps H
   positive definite; Alg. 2 stores every pair.
 * No line search (do_linesearch = false; the paper's runs use a fixed step).
+* The trial point u + nu z is projected onto the bounds as well, and the stored
+  pair is (u_trial - u, G_z - G_u): the bounds exist to keep the wave simulation
+  stable, which the trial evaluation needs too.  With inactive bounds this is
+  Alg. 2 as printed.
 """
 from __future__ import annotations
 
@@ -80,9 +84,10 @@ def slbfgs(u, estimator, nu, n_evl, m=64, h0=None, weight=lambda i: float(i) ** 
         F_u, G_u = estimator(u, theta(i), i)
         evl += 1
         z = -two_loop(G_u, S, Y, scaling(S, Y, h0))
-        F_z, G_z = estimator(u + nu * z, theta(i), i)
+        u_trial = np.clip(u + nu * z, u_min, u_max)
+        F_z, G_z = estimator(u_trial, theta(i), i)
         evl += 1
-        push_pair(S, Y, nu * z, G_z - G_u, m)
+        push_pair(S, Y, u_trial - u, G_z - G_u, m)
         z = z - two_loop(G_z, S, Y, scaling(S, Y, h0))
         u = np.clip(u + nu * z, u_min, u_max)
         J = min(F_u, F_z)

@@ -34,7 +34,9 @@ C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_g
              "fwi_plan_profile_read", "fwi_plan_set_schedule", "fwi_plan_get_schedule",
              "fwi_adjoint_source_noalloc", "fwi_batch_create",
              "fwi_batch_gradient", "fwi_batch_nodes", "fwi_batch_destroy", "fwi_plan_destroy",
-             "fwi_status_string", "fwi_last_cuda_error")
+             "fwi_status_string", "fwi_last_cuda_error", "fwi_lbfgs_create", "fwi_lbfgs_bind_workspace",
+             "fwi_lbfgs_push", "fwi_lbfgs_apply", "fwi_lbfgs_size", "fwi_lbfgs_destroy", "fwi_vec_step_project",
+             "fwi_vec_accumulate", "fwi_param_to_speed", "fwi_grad_to_param")
 
 NOALLOC_MAX_PARTIALS = 8192
 
@@ -127,6 +129,27 @@ def lib():
         L.fwi_last_cuda_error.restype = ctypes.c_char_p
         L.fwi_status_string.argtypes = [ctypes.c_int]
         L.fwi_status_string.restype = ctypes.c_char_p
+        dbl = ctypes.c_double
+        L.fwi_lbfgs_create.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(vp)]
+        L.fwi_lbfgs_create.restype = ctypes.c_int
+        L.fwi_lbfgs_bind_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+        L.fwi_lbfgs_bind_workspace.restype = ctypes.c_int
+        L.fwi_lbfgs_push.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i32)]
+        L.fwi_lbfgs_push.restype = ctypes.c_int
+        L.fwi_lbfgs_apply.argtypes = [vp, vp, dbl, vp, vp]
+        L.fwi_lbfgs_apply.restype = ctypes.c_int
+        L.fwi_lbfgs_size.argtypes = [vp]
+        L.fwi_lbfgs_size.restype = i32
+        L.fwi_lbfgs_destroy.argtypes = [vp]
+        L.fwi_lbfgs_destroy.restype = ctypes.c_int
+        L.fwi_vec_step_project.argtypes = [i64, vp, vp, dbl, dbl, dbl, vp]
+        L.fwi_vec_step_project.restype = ctypes.c_int
+        L.fwi_vec_accumulate.argtypes = [i64, vp, vp, dbl, vp]
+        L.fwi_vec_accumulate.restype = ctypes.c_int
+        L.fwi_param_to_speed.argtypes = [i64, i32, vp, vp, vp]
+        L.fwi_param_to_speed.restype = ctypes.c_int
+        L.fwi_grad_to_param.argtypes = [i64, i32, vp, vp, vp, vp]
+        L.fwi_grad_to_param.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -165,6 +188,51 @@ def fwi_gradient_delayed(plan, c_ptr, w_ptr, d_ptr, K, obs_ptr, obs_encoded, obs
                          traces_ptr, stream) -> int:
     return lib().fwi_gradient_delayed(plan, c_ptr, w_ptr, d_ptr, K, obs_ptr, obs_encoded, obs_nt, misfit_ptr,
                                       grad_ptr, traces_ptr, stream)
+
+
+def fwi_lbfgs_create(n, m):
+    ws = ctypes.c_size_t(0)
+    h = ctypes.c_void_p(0)
+    st = lib().fwi_lbfgs_create(n, m, ctypes.byref(ws), ctypes.byref(h))
+    return st, h, ws.value
+
+
+def fwi_lbfgs_bind_workspace(h, ptr: int, nbytes: int) -> int:
+    return lib().fwi_lbfgs_bind_workspace(h, ctypes.c_void_p(ptr), nbytes)
+
+
+def fwi_lbfgs_push(h, s_ptr, y_ptr, stream):
+    stored = ctypes.c_int32(0)
+    st = lib().fwi_lbfgs_push(h, s_ptr, y_ptr, stream, ctypes.byref(stored))
+    return st, bool(stored.value)
+
+
+def fwi_lbfgs_apply(h, g_ptr, h0, out_ptr, stream) -> int:
+    return lib().fwi_lbfgs_apply(h, g_ptr, h0, out_ptr, stream)
+
+
+def fwi_lbfgs_size(h) -> int:
+    return lib().fwi_lbfgs_size(h)
+
+
+def fwi_lbfgs_destroy(h) -> int:
+    return lib().fwi_lbfgs_destroy(h)
+
+
+def fwi_vec_step_project(n, u_ptr, z_ptr, nu, u_min, u_max, stream) -> int:
+    return lib().fwi_vec_step_project(n, u_ptr, z_ptr, nu, u_min, u_max, stream)
+
+
+def fwi_vec_accumulate(n, acc_ptr, u_ptr, w, stream) -> int:
+    return lib().fwi_vec_accumulate(n, acc_ptr, u_ptr, w, stream)
+
+
+def fwi_param_to_speed(n, kind, u_ptr, c_ptr, stream) -> int:
+    return lib().fwi_param_to_speed(n, kind, u_ptr, c_ptr, stream)
+
+
+def fwi_grad_to_param(n, kind, c_ptr, gc_ptr, gu_ptr, stream) -> int:
+    return lib().fwi_grad_to_param(n, kind, c_ptr, gc_ptr, gu_ptr, stream)
 
 
 def fwi_plan_status(plan) -> int:

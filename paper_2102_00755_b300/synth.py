@@ -275,6 +275,16 @@ def config4() -> Workload:
     return phantom_workload("diff-96x96x48", 96, 96, 48, 1000, 32, 128, 1, 100, (101,))
 
 
+def encoding_draws(seed: int, K: int, n_src: int, tau: int = 0):
+    """Rademacher weights [K][n_src] and delays [K][n_src] (whole time steps, d ~ U[0, 1]
+    times tau, rounded; zero when tau = 0) of the stochastic approximation number `seed`
+    of the encoded gradient estimator (Sec. 3.2, Eq. 13)."""
+    rng = np.random.default_rng(seed)
+    w = np.where(rng.integers(0, 2, size=(K, n_src)) == 1, 1.0, -1.0)
+    d = np.rint(rng.uniform(0.0, 1.0, size=(K, n_src)) * tau).astype(np.int32)
+    return w, d
+
+
 def smooth_direction(wl: Workload, seed: int, n_terms: int = 4) -> np.ndarray:
     """Seeded smooth perturbation direction supported in Gamma: a sum of n_terms
     low-order 3D cosines (wavenumbers 0..3 per axis, random phases) restricted to
