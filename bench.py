@@ -423,9 +423,15 @@ def main():
     bpv = alg_bytes_per_voxel(dominant, wl.nx)
     alg_bytes = bpv * wl.n_vox * kern_sims
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
+    # the whole step: algorithmic bytes of all four kernels per voxel-step over the step time
+    # (with two stream groups, launches of different kernels overlap, so a kernel's own event
+    # time includes time shared with the other group's kernels)
+    step_bpv = sum(alg_bytes_per_voxel(k, wl.nx) for k in fwi.KERNELS)
+    step_gbs = step_bpv * vsteps * args.steps / (tot_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm,
                 "peak_kind": kind, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
                 "traffic": None, "alg_bytes_per_voxel": bpv,
+                "step": {"alg_bytes_per_voxel_step": step_bpv, "achieved": step_gbs, "frac": step_gbs / hbm},
                 "avg_launch_ms": kern_ms / max(kern_launches, 1), "launches_timed": kern_launches,
                 "kernel_share_of_step": {k: v / sum(share_ms.values()) for k, v in share_ms.items()}}
 

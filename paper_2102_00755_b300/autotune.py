@@ -17,10 +17,10 @@ import torch
 
 from . import fwi
 
-CANDIDATES = [dict(specialized=s, radix_order=r, z_tile=t, split_plane=sp)
-              for sp in (0, 1) for s in (2, 1, 0) for r in (0, 1, 2) for t in (32, 16)
-              if not (s >= 1 and r != 0) and not (sp == 1 and s == 1)]
-KNOBS = ("specialized", "radix_order", "z_tile", "split_plane")
+CANDIDATES = [dict(specialized=s, radix_order=r, z_tile=t, split_plane=sp, stream_groups=g)
+              for sp in (0, 1) for s in (2, 1, 0) for r in (0, 1, 2) for t in (32, 16) for g in (1, 2)
+              if not (s >= 1 and r != 0) and not (sp == 1 and s == 1) and not (g == 2 and s != 2)]
+KNOBS = ("specialized", "radix_order", "z_tile", "split_plane", "stream_groups")
 
 
 def cache_path() -> str:
@@ -42,7 +42,7 @@ def key_of(nx, ny, nz, K) -> str:
 
 def set_schedule(plan, sched: dict) -> int:
     s = fwi.fwi_schedule(sched["specialized"], sched["radix_order"], sched["z_tile"],
-                         sched.get("split_plane", 0))
+                         sched.get("split_plane", 0), sched.get("stream_groups", 1))
     return fwi.lib().fwi_plan_set_schedule(plan.handle, ctypes.byref(s))
 
 
@@ -50,7 +50,7 @@ def get_schedule(plan) -> dict:
     s = fwi.fwi_schedule()
     fwi._check(fwi.lib().fwi_plan_get_schedule(plan.handle, ctypes.byref(s)), "fwi_plan_get_schedule")
     return dict(specialized=s.specialized, radix_order=s.radix_order, z_tile=s.z_tile,
-                split_plane=s.split_plane)
+                split_plane=s.split_plane, stream_groups=s.stream_groups)
 
 
 def tune(wl, K: int = 1, steps: int = 24, reps: int = 3, device="cuda", save=True, verbose=False) -> dict:

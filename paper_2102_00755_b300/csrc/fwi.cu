@@ -161,9 +161,9 @@ __global__ void k_misfit_final(const double* dpart, int nblk, int K, double* mis
 // grad_k(Gamma) += 2/(dt c0^3) (p+ - 2 p0 + p-) p_adj  (FP64 accumulator, Alg. 1)
 __global__ void k_accumulate(const float* __restrict__ ring, const float* __restrict__ pa,
                              const float* __restrict__ coefG, int n_gamma, int sa, int sb, int sc,
-                             double* __restrict__ acc, const int* bad) {
+                             double* __restrict__ acc, const int* bad, int k0) {
   if (*bad) return;
-  const int k = blockIdx.y;
+  const int k = k0 + blockIdx.y;
   const float* rk = ring + (size_t)k * 3 * n_gamma;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_gamma; j += gridDim.x * blockDim.x) {
     const float d2 = rk[(size_t)sa * n_gamma + j] - 2.f * rk[(size_t)sb * n_gamma + j] +
@@ -328,6 +328,9 @@ struct fwi_plan {
   size_t ws_bytes = 0;
   cudaStream_t last = nullptr;
   bool used = false;
+  // second stream of the two-group form, with its fork and join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // profiling hook
   int prof_mask = 0;
   bool prof_on = false;
@@ -824,11 +827,31 @@ fwi_status run_forward(fwi_plan* p, const float* w, const int* delay, int K, boo
     fwi_status s = zero_sim(p, k, st);
     if (s != FWI_OK) return s;
   }
-  for (int n = 0; n < q.nt; ++n) {
-    for (int k = 0; k < K; ++k) P.tidx[k] = n;
-    const fwi_status s = launch_step(p, P, st);
-    if (s != FWI_OK) return s;
+  const int G = (p->sched.stream_groups == 2 && K >= 2) ? 2 : 1;
+  if (G == 1) {
+    for (int n = 0; n < q.nt; ++n) {
+      for (int k = 0; k < K; ++k) P.tidx[k] = n;
+      const fwi_status s = launch_step(p, P, st);
+      if (s != FWI_OK) return s;
+    }
+    return FWI_OK;
   }
+  // two groups of super-shots on two streams, forked from and joined to `st`
+  const int KA = (K + 1) / 2;
+  StepParams A = P, B = P;
+  A.nsims = KA;
+  B.nsims = K - KA;
+  for (int k = 0; k < K - KA; ++k) B.sims[k] = P.sims[KA + k];
+  CK(cudaEventRecord(p->ev_fork, st));
+  CK(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  for (int n = 0; n < q.nt; ++n) {
+    for (int k = 0; k < K; ++k) A.tidx[k] = B.tidx[k] = n;
+    fwi_status s = launch_step(p, A, st);
+    if (s != FWI_OK) return s;
+    if ((s = launch_step(p, B, p->side)) != FWI_OK) return s;
+  }
+  CK(cudaEventRecord(p->ev_join, p->side));
+  CK(cudaStreamWaitEvent(st, p->ev_join, 0));
   return FWI_OK;
 }
 
@@ -960,8 +983,8 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   // default schedule: two-step kernels where built (whole planes, else split planes),
   // else the compile-time or runtime transforms (whole planes, else split planes)
   bool placed = false;
-  for (const fwi_schedule sc : {fwi_schedule{2, 0, 32, 0}, fwi_schedule{2, 0, 32, 1}, fwi_schedule{1, 0, 32, 0},
-                                fwi_schedule{1, 0, 32, 1}}) {
+  for (const fwi_schedule sc : {fwi_schedule{2, 0, 32, 0, 2}, fwi_schedule{2, 0, 32, 1, 2},
+                                fwi_schedule{1, 0, 32, 0, 2}, fwi_schedule{1, 0, 32, 1, 2}}) {
     p->sched = sc;
     if (apply_schedule(p) == FWI_OK) {
       placed = true;
@@ -1054,6 +1077,9 @@ fwi_status fwi_plan_bind_workspace(fwi_plan* p, void* dev_ptr, size_t bytes) {
   CK(upc(p->lay, p->o_lay_ptr, p->o_lay_vox, p->o_lay_pf));
   CK(upc(p->gam, p->o_gam_ptr, p->o_gam_vox, p->o_gam_pf));
   CK(up(p->o_wav, p->wavelet.data(), p->wavelet.size() * 4));
+  if (!p->side) CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+  if (!p->ev_fork) CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  if (!p->ev_join) CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
   set_attrs(p);
   CK(cudaGetLastError());
   return FWI_OK;
@@ -1179,29 +1205,51 @@ fwi_status gradient_impl(fwi_plan* p, const float* c, const float* weights, cons
   const bool exact = q.pairing == FWI_PAIRING_EXACT;
   const int nit = exact ? Nt + 1 : Nt - 1;
   const int nblk = (q.n_gamma + 255) / 256;
-  for (int it = 0; it < nit; ++it) {
+  // shots [k0, k0 + nk) advance on stream gs: their adjoint simulations (k) and TR
+  // simulations (K + k) in one launch sequence, then their Gamma accumulation
+  auto iterate = [&](int it, int k0, int nk, cudaStream_t gs) -> fwi_status {
     const int qi = exact ? it : it + 1;    // row of Q injected by this adjoint step
     const int m = it + 2;                  // TR state produced in this iteration
     const int slot = m % 3;
     StepParams S = P;
-    S.nsims = K;
-    for (int k = 0; k < K; ++k) S.tidx[k] = qi;
+    S.nsims = nk;
+    for (int k = 0; k < nk; ++k) {
+      S.sims[k] = P.sims[k0 + k];
+      S.tidx[k] = qi;
+    }
     if (m <= Nt) {
-      S.nsims = 2 * K;
-      for (int k = 0; k < K; ++k) {
-        S.tidx[K + k] = m;
-        S.slot[K + k] = slot;
+      S.nsims = 2 * nk;
+      for (int k = 0; k < nk; ++k) {
+        S.sims[nk + k] = P.sims[K + k0 + k];
+        S.tidx[nk + k] = m;
+        S.slot[nk + k] = slot;
       }
     } else {
-      for (int k = 0; k < K; ++k)
+      for (int k = k0; k < k0 + nk; ++k)
         CK(cudaMemsetAsync(at<float>(p, p->o_ring) + ((size_t)k * 3 + slot) * q.n_gamma, 0,
-                           (size_t)q.n_gamma * 4, st));
+                           (size_t)q.n_gamma * 4, gs));
     }
-    if ((s = launch_step(p, S, st)) != FWI_OK) return s;
-    k_accumulate<<<dim3(nblk, K), 256, 0, st>>>(at<float>(p, p->o_ring), at<float>(p, p->o_pa),
-                                                at<float>(p, p->o_coefG), q.n_gamma, it % 3, (it + 1) % 3,
-                                                (it + 2) % 3, at<double>(p, p->o_acc), at<int>(p, p->o_bad));
+    fwi_status r = launch_step(p, S, gs);
+    if (r != FWI_OK) return r;
+    k_accumulate<<<dim3(nblk, nk), 256, 0, gs>>>(at<float>(p, p->o_ring), at<float>(p, p->o_pa),
+                                                 at<float>(p, p->o_coefG), q.n_gamma, it % 3, (it + 1) % 3,
+                                                 (it + 2) % 3, at<double>(p, p->o_acc), at<int>(p, p->o_bad), k0);
     LAUNCHED("k_accumulate");
+    return FWI_OK;
+  };
+  const int G = (p->sched.stream_groups == 2 && K >= 2) ? 2 : 1;
+  const int KA = G == 2 ? (K + 1) / 2 : K;
+  if (G == 2) {
+    CK(cudaEventRecord(p->ev_fork, st));
+    CK(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  }
+  for (int it = 0; it < nit; ++it) {
+    if ((s = iterate(it, 0, KA, st)) != FWI_OK) return s;
+    if (G == 2 && (s = iterate(it, KA, K - KA, p->side)) != FWI_OK) return s;
+  }
+  if (G == 2) {
+    CK(cudaEventRecord(p->ev_join, p->side));
+    CK(cudaStreamWaitEvent(st, p->ev_join, 0));
   }
   // mean over shots, scaled to dD/dc if requested
   const double scale = q.c_rec > 0 ? q.dx * q.c_rec / 2.0 : 1.0;
@@ -1439,7 +1487,8 @@ fwi_status fwi_batch_destroy(fwi_batch* b) {
 fwi_status fwi_plan_set_schedule(fwi_plan* p, const fwi_schedule* sc) {
   if (!p || !sc) return FWI_EINVAL;
   if (sc->specialized < 0 || sc->specialized > 2 || sc->radix_order < 0 || sc->radix_order > 2 ||
-      (sc->z_tile != 16 && sc->z_tile != 32) || (sc->split_plane != 0 && sc->split_plane != 1))
+      (sc->z_tile != 16 && sc->z_tile != 32) || (sc->split_plane != 0 && sc->split_plane != 1) ||
+      (sc->stream_groups != 1 && sc->stream_groups != 2))
     return FWI_EINVAL;
   const fwi_schedule old = p->sched;
   p->sched = *sc;
@@ -1459,8 +1508,12 @@ fwi_status fwi_plan_get_schedule(const fwi_plan* p, fwi_schedule* sc) {
 }
 
 fwi_status fwi_plan_destroy(fwi_plan* p) {
-  if (p)
+  if (p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+    if (p->side) cudaStreamDestroy(p->side);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+  }
   delete p;
   return FWI_OK;
 }

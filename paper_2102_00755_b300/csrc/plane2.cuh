@@ -91,6 +91,29 @@ __device__ __forceinline__ void p2_fetch_rows(float2* Gb, const float* __restric
   cp_async_commit();
 }
 
+#ifndef P2_TW_POW
+#define P2_TW_POW 1
+#endif
+#ifndef P2_STAGE_STATE
+#define P2_STAGE_STATE 1
+#endif
+
+__host__ __device__ constexpr int hibit(int k) { return k <= 1 ? k : 2 * hibit(k / 2); }
+
+// w[k] = tab[base * k * step]... for k < M: the step-A twiddles of one task.  With
+// P2_TW_POW the powers of two are read from the table and the others formed as
+// products (fewer shared-memory loads, a few ulp of extra rounding).
+template <int M>
+__device__ __forceinline__ void tw_row(const float2* tab, int stride, float2 (&w)[M]) {
+  w[0] = make_float2(1.f, 0.f);
+  sfor<1, M>([&](auto K) {
+    constexpr int k = decltype(K)::value;
+    constexpr int h = hibit(k);
+    if constexpr (P2_TW_POW && h != k) w[k] = cmul(w[h], w[k - h]);
+    else w[k] = tab[k * stride];
+  });
+}
+
 template <class G>
 __device__ __forceinline__ float2* p2_row(float2* buf, int ky) {
   return buf + (ky >> 1) * G::PST + (ky & 1) * G::HX;
@@ -137,9 +160,11 @@ __device__ __forceinline__ void p2_yinv_a(float2* S, const float2* src, int fk,
       });
     }
     RDft<G::BY1, true>::run(a);
+    float2 w[G::BY1];
+    tw_row<G::BY1>(twy, j2, w);
     sfor<1, G::BY1>([&](auto K1) {
       constexpr int k1 = decltype(K1)::value;
-      a[k1] = cmulc(a[k1], twy[j2 * k1]);
+      a[k1] = cmulc(a[k1], w[k1]);
     });
     sfor<0, G::BY1>([&](auto K1) {
       constexpr int k1 = decltype(K1)::value;
@@ -200,9 +225,11 @@ __device__ __forceinline__ void p2_xinv_a(const float2* X, float2* S, const floa
       z[j1] = make_float2(a.x - b.y, a.y + b.x);
     });
     RDft<G::AX1, true>::run(z);
+    float2 w[G::AX1];
+    tw_row<G::AX1>(twx, j2, w);
     sfor<1, G::AX1>([&](auto K1) {
       constexpr int k1 = decltype(K1)::value;
-      z[k1] = cmulc(z[k1], twx[j2 * k1]);
+      z[k1] = cmulc(z[k1], w[k1]);
     });
     float2* o = S + p * G::PST + j2;
     sfor<0, G::AX1>([&](auto K1) {
@@ -217,10 +244,11 @@ template <class G>
 __device__ __forceinline__ void p2_xfwd_a(float2* z, int p, int k1, float2* out, const float2* twxT) {
   RDft<G::AX2, false>::run(z);
   float2* o = out + p * G::PST + k1;
+  float2 w[G::AX2];
+  tw_row<G::AX2>(twxT + k1, G::AX1, w);
   sfor<0, G::AX2>([&](auto K1P) {
     constexpr int k1p = decltype(K1P)::value;
-    const float2 w = k1p == 0 ? make_float2(1.f, 0.f) : twxT[k1p * G::AX1 + k1];
-    o[k1p * G::PB] = k1p == 0 ? z[k1p] : cmul(z[k1p], w);
+    o[k1p * G::PB] = k1p == 0 ? z[k1p] : cmul(z[k1p], w[k1p]);
   });
 }
 
@@ -257,9 +285,11 @@ __device__ __forceinline__ void p2_yfwd_a(const float2* in, float2* out, const f
                        : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     });
     RDft<G::BY1, false>::run(a);
+    float2 w[G::BY1];
+    tw_row<G::BY1>(twy, j2, w);
     sfor<1, G::BY1>([&](auto K1) {
       constexpr int k1 = decltype(K1)::value;
-      a[k1] = cmul(a[k1], twy[j2 * k1]);
+      a[k1] = cmul(a[k1], w[k1]);
     });
     sfor<0, G::BY1>([&](auto K1) {
       constexpr int k1 = decltype(K1)::value;
@@ -419,14 +449,15 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mom(const __gr
     __syncthreads();
     p2_yinv_a<G>(S, G::STAGE ? Gb : src_of(comp), comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.ap[comp], twy);
     __syncthreads();
-    if constexpr (G::STAGE) p2_fetch_rows<G>(Gb, vg);      // overlaps phases 2 and 3
+    if constexpr (G::STAGE && P2_STAGE_STATE) p2_fetch_rows<G>(Gb, vg);      // overlaps phases 2 and 3
     p2_y_b<G, true>(S, X, nullptr);
     __syncthreads();
     p2_xinv_a<G>(X, S, twx);
     if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
-    p2_mom_update<G>(S, X, twxT, vg, G::STAGE ? reinterpret_cast<const float*>(Gb) : vg,
-                     G::STAGE ? G::RS : NX, P.lams[comp], comp, lz, P.dt_over_rho0, NY);
+    constexpr bool SS = G::STAGE && P2_STAGE_STATE;
+    p2_mom_update<G>(S, X, twxT, vg, SS ? reinterpret_cast<const float*>(Gb) : vg, SS ? G::RS : NX,
+                     P.lams[comp], comp, lz, P.dt_over_rho0, NY);
     __syncthreads();
     if constexpr (G::STAGE) {                               // next spectrum overlaps phases 5-7
       if (cc < 2) p2_fetch_spec<G>(Gb, src_of(cc == 0 ? 0 : 1));
@@ -470,14 +501,15 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
     __syncthreads();
     p2_yinv_a<G>(S, src, comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.am[comp], twy);
     __syncthreads();
-    if constexpr (G::STAGE) p2_fetch_rows<G>(Gb, rg);      // overlaps phases 2 and 3
+    if constexpr (G::STAGE && P2_STAGE_STATE) p2_fetch_rows<G>(Gb, rg);      // overlaps phases 2 and 3
     p2_y_b<G, true>(S, X, nullptr);
     __syncthreads();
     p2_xinv_a<G>(X, S, twx);
     if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
-    const float* rin = G::STAGE ? reinterpret_cast<const float*>(Gb) : rg;
-    const int rs = G::STAGE ? G::RS : NX;
+    constexpr bool SS = G::STAGE && P2_STAGE_STATE;
+    const float* rin = SS ? reinterpret_cast<const float*>(Gb) : rg;
+    const int rs = SS ? G::RS : NX;
     if (cc < 2) {
       p2_fetch_spec<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff);   // overlaps phase 4
       p2_mass_update<G, false>(S, nullptr, rg, rin, rs, P.lam[comp], comp, lz, P.dt_rho0, nullptr, nullptr,
@@ -663,9 +695,11 @@ __global__ void __launch_bounds__(Z2<NZ, TZ>::NT) k_zpass2(const __grid_constant
     {
       const int ml = mlA, j2 = j2A;
       RDft<N1, false>::run(a);
+      float2 w[N1];
+      tw_row<N1>(tw, j2, w);
       sfor<0, N1>([&](auto K1) {
         constexpr int k1 = decltype(K1)::value;
-        b0[(j2 + N2 * k1) * TZ + ml] = k1 == 0 ? a[k1] : cmul(a[k1], tw[j2 * k1]);
+        b0[(j2 + N2 * k1) * TZ + ml] = k1 == 0 ? a[k1] : cmul(a[k1], w[k1]);
       });
     }
     __syncthreads();
@@ -689,16 +723,18 @@ __global__ void __launch_bounds__(Z2<NZ, TZ>::NT) k_zpass2(const __grid_constant
         }
       });
       // inverse: the held values are the stride-N1 subsequence kz = k1 + N1 k2
+      float2 w[N2];
+      tw_row<N2>(twT + k1, N1, w);
       RDft<N2, true>::run(x);
       sfor<0, N2>([&](auto K1P) {
         constexpr int k1p = decltype(K1P)::value;
-        b1[(k1p * N1 + k1) * TZ + ml] = k1p == 0 ? x[k1p] : cmulc(x[k1p], twT[k1p * N1 + k1]);
+        b1[(k1p * N1 + k1) * TZ + ml] = k1p == 0 ? x[k1p] : cmulc(x[k1p], w[k1p]);
       });
       if constexpr (MODE == 0) {
         RDft<N2, true>::run(r);
         sfor<0, N2>([&](auto K1P) {
           constexpr int k1p = decltype(K1P)::value;
-          b2[(k1p * N1 + k1) * TZ + ml] = k1p == 0 ? r[k1p] : cmulc(r[k1p], twT[k1p * N1 + k1]);
+          b2[(k1p * N1 + k1) * TZ + ml] = k1p == 0 ? r[k1p] : cmulc(r[k1p], w[k1p]);
         });
       }
     }

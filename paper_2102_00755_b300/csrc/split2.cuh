@@ -70,10 +70,12 @@ __global__ void __launch_bounds__(Y2<NY, TY>::NT) k_ypass2(const __grid_constant
     __syncthreads();   // twiddles staged; the previous slot's buffer consumed
     if (N2 > 16 && s > 0) load_a(s);
     RDft<N1, INV>::run(a);
+    float2 w[N1];
+    tw_row<N1>(tw, j2A, w);
     sfor<0, N1>([&](auto K1) {
       constexpr int k1 = decltype(K1)::value;
       float2 v = a[k1];
-      if (k1 > 0) v = INV ? cmulc(v, tw[j2A * k1]) : cmul(v, tw[j2A * k1]);
+      if (k1 > 0) v = INV ? cmulc(v, w[k1]) : cmul(v, w[k1]);
       b[(j2A + N2 * k1) * TY + mlA] = v;
     });
     __syncthreads();

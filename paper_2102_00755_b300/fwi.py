@@ -54,7 +54,7 @@ class FwiError(RuntimeError):
 
 class fwi_schedule(ctypes.Structure):
     _fields_ = [("specialized", ctypes.c_int32), ("radix_order", ctypes.c_int32), ("z_tile", ctypes.c_int32),
-                ("split_plane", ctypes.c_int32)]
+                ("split_plane", ctypes.c_int32), ("stream_groups", ctypes.c_int32)]
 
 
 class fwi_problem(ctypes.Structure):

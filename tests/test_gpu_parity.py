@@ -243,3 +243,22 @@ def test_two_step_split_plane_gradient_parity(shape, pairing):
         assert oc.rel(traces[k].cpu().numpy(), f_ref[k]) < TOL_TRACES
     assert np.all(np.abs(D.cpu().numpy() - D_ref) <= TOL_MISFIT * np.abs(D_ref))
     assert oc.rel(g.cpu().numpy().reshape(wl.shape), g_ref) < TOL_GRAD
+
+
+def test_two_stream_groups_are_bit_identical():
+    """stream_groups = 2 (super-shots split over two streams) changes only the launch
+    grouping: traces, misfits and gradients equal those of one group bit for bit."""
+    from paper_2102_00755_b300 import autotune
+    wl, f_obs = oc.small_case()
+    plan = fwi.Plan.from_workload(wl, pairing="literal", max_shots=len(wl.weights))
+    c, w, o = dev(wl.c_model), dev(wl.weights), dev(f_obs)
+    outs = []
+    for g in (1, 2):
+        sched = dict(specialized=1, radix_order=0, z_tile=32, split_plane=0, stream_groups=g)
+        assert autotune.set_schedule(plan, sched) == fwi.FWI_OK
+        tr = plan.forward(c, w).clone()
+        D, grad = plan.gradient(c, w, o)
+        outs.append((tr, D.clone(), grad.clone()))
+    assert plan.status() == fwi.FWI_OK
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
