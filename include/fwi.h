@@ -231,13 +231,13 @@ int64_t fwi_plan_launches(const fwi_plan *plan, int32_t K, int32_t gradient);
  *   split_plane: 0 = one CTA transforms a whole z-plane in shared memory; 1 = the XY
  *                work of a plane is split into column (y) and row-pair (x) passes
  *                through global memory (always used when a plane does not fit)
- *   stream_groups: 1 = all simulations of a call advance in one launch sequence; 2 =
- *                the super-shots are split into two halves (for gradients: each shot's
- *                adjoint and TR simulations together) that advance on two streams, so
- *                that kernels of one half fill SMs the other leaves idle.  Results are
- *                bit-identical; used only when K >= 2.
- * fwi_plan_create picks the first of {2, 0, 32, 0, 2}, {2, 0, 32, 1, 2}, {1, 0, 32, 0, 2},
- * {1, 0, 32, 1, 2} that applies (split planes only where a plane does not fit).  Setting a schedule keeps the workspace size;
+ *   stream_groups: 1 = all simulations of a call advance in one launch sequence; 2 or
+ *                4 = the super-shots are split into that many groups (at most K; for
+ *                gradients each shot's adjoint and TR simulations stay together) that
+ *                advance on separate streams, so that kernels of one group fill SMs the
+ *                others leave idle.  Results are bit-identical.
+ * fwi_plan_create picks the first of {2, 0, 32, 0, 4}, {2, 0, 32, 1, 4}, {1, 0, 32, 0, 4},
+ * {1, 0, 32, 1, 4} that applies (split planes only where a plane does not fit).  Setting a schedule keeps the workspace size;
  * it may be changed after binding (between calls).  Results differ only by FP32
  * rounding order.  Errors: FWI_EINVAL (bad values), FWI_ENOTSUP (the shared memory
  * the schedule needs exceeds the device limit).

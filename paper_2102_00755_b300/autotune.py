@@ -18,8 +18,8 @@ import torch
 from . import fwi
 
 CANDIDATES = [dict(specialized=s, radix_order=r, z_tile=t, split_plane=sp, stream_groups=g)
-              for sp in (0, 1) for s in (2, 1, 0) for r in (0, 1, 2) for t in (32, 16) for g in (1, 2)
-              if not (s >= 1 and r != 0) and not (sp == 1 and s == 1) and not (g == 2 and s != 2)]
+              for sp in (0, 1) for s in (2, 1, 0) for r in (0, 1, 2) for t in (32, 16) for g in (1, 2, 4)
+              if not (s >= 1 and r != 0) and not (sp == 1 and s == 1) and not (g > 1 and s != 2)]
 KNOBS = ("specialized", "radix_order", "z_tile", "split_plane", "stream_groups")
 
 

@@ -328,9 +328,10 @@ struct fwi_plan {
   size_t ws_bytes = 0;
   cudaStream_t last = nullptr;
   bool used = false;
-  // second stream of the two-group form, with its fork and join events
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // extra streams of the stream-group form, with the fork event and one join event each
+  static constexpr int kMaxGroups = 4;
+  cudaStream_t side[kMaxGroups - 1] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kMaxGroups - 1] = {};
   // profiling hook
   int prof_mask = 0;
   bool prof_on = false;
@@ -810,6 +811,24 @@ fwi_status prepare(fwi_plan* p, const float* c, cudaStream_t st) {
   return FWI_OK;
 }
 
+// Stream groups: shots [g*KG, min(K, (g+1)*KG)) of group g advance on stream g (0 = the
+// caller's stream), forked from and joined to it.
+int group_count(const fwi_plan* p, int K) { return std::max(1, std::min(p->sched.stream_groups, K)); }
+cudaStream_t group_stream(const fwi_plan* p, int g, cudaStream_t st) { return g == 0 ? st : p->side[g - 1]; }
+fwi_status fork_groups(fwi_plan* p, int G, cudaStream_t st) {
+  if (G < 2) return FWI_OK;
+  CK(cudaEventRecord(p->ev_fork, st));
+  for (int g = 1; g < G; ++g) CK(cudaStreamWaitEvent(p->side[g - 1], p->ev_fork, 0));
+  return FWI_OK;
+}
+fwi_status join_groups(fwi_plan* p, int G, cudaStream_t st) {
+  for (int g = 1; g < G; ++g) {
+    CK(cudaEventRecord(p->ev_join[g - 1], p->side[g - 1]));
+    CK(cudaStreamWaitEvent(st, p->ev_join[g - 1], 0));
+  }
+  return FWI_OK;
+}
+
 fwi_status run_forward(fwi_plan* p, const float* w, const int* delay, int K, bool record_layer,
                        float* traces, cudaStream_t st) {
   const fwi_problem& q = p->prob;
@@ -827,32 +846,23 @@ fwi_status run_forward(fwi_plan* p, const float* w, const int* delay, int K, boo
     fwi_status s = zero_sim(p, k, st);
     if (s != FWI_OK) return s;
   }
-  const int G = (p->sched.stream_groups == 2 && K >= 2) ? 2 : 1;
-  if (G == 1) {
-    for (int n = 0; n < q.nt; ++n) {
-      for (int k = 0; k < K; ++k) P.tidx[k] = n;
-      const fwi_status s = launch_step(p, P, st);
-      if (s != FWI_OK) return s;
-    }
-    return FWI_OK;
+  const int G = group_count(p, K), KG = (K + G - 1) / G;
+  StepParams Q[fwi_plan::kMaxGroups];
+  for (int g = 0; g < G; ++g) {
+    Q[g] = P;
+    Q[g].nsims = std::max(0, std::min(K, (g + 1) * KG) - g * KG);
+    for (int k = 0; k < Q[g].nsims; ++k) Q[g].sims[k] = P.sims[g * KG + k];
   }
-  // two groups of super-shots on two streams, forked from and joined to `st`
-  const int KA = (K + 1) / 2;
-  StepParams A = P, B = P;
-  A.nsims = KA;
-  B.nsims = K - KA;
-  for (int k = 0; k < K - KA; ++k) B.sims[k] = P.sims[KA + k];
-  CK(cudaEventRecord(p->ev_fork, st));
-  CK(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  fwi_status s = fork_groups(p, G, st);
+  if (s != FWI_OK) return s;
   for (int n = 0; n < q.nt; ++n) {
-    for (int k = 0; k < K; ++k) A.tidx[k] = B.tidx[k] = n;
-    fwi_status s = launch_step(p, A, st);
-    if (s != FWI_OK) return s;
-    if ((s = launch_step(p, B, p->side)) != FWI_OK) return s;
+    for (int g = 0; g < G; ++g) {
+      if (Q[g].nsims == 0) continue;
+      for (int k = 0; k < Q[g].nsims; ++k) Q[g].tidx[k] = n;
+      if ((s = launch_step(p, Q[g], group_stream(p, g, st))) != FWI_OK) return s;
+    }
   }
-  CK(cudaEventRecord(p->ev_join, p->side));
-  CK(cudaStreamWaitEvent(st, p->ev_join, 0));
-  return FWI_OK;
+  return join_groups(p, G, st);
 }
 
 fwi_status check_call(fwi_plan* p, int K) {
@@ -983,8 +993,8 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   // default schedule: two-step kernels where built (whole planes, else split planes),
   // else the compile-time or runtime transforms (whole planes, else split planes)
   bool placed = false;
-  for (const fwi_schedule sc : {fwi_schedule{2, 0, 32, 0, 2}, fwi_schedule{2, 0, 32, 1, 2},
-                                fwi_schedule{1, 0, 32, 0, 2}, fwi_schedule{1, 0, 32, 1, 2}}) {
+  for (const fwi_schedule sc : {fwi_schedule{2, 0, 32, 0, 4}, fwi_schedule{2, 0, 32, 1, 4},
+                                fwi_schedule{1, 0, 32, 0, 4}, fwi_schedule{1, 0, 32, 1, 4}}) {
     p->sched = sc;
     if (apply_schedule(p) == FWI_OK) {
       placed = true;
@@ -1077,9 +1087,11 @@ fwi_status fwi_plan_bind_workspace(fwi_plan* p, void* dev_ptr, size_t bytes) {
   CK(upc(p->lay, p->o_lay_ptr, p->o_lay_vox, p->o_lay_pf));
   CK(upc(p->gam, p->o_gam_ptr, p->o_gam_vox, p->o_gam_pf));
   CK(up(p->o_wav, p->wavelet.data(), p->wavelet.size() * 4));
-  if (!p->side) CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+  for (int g = 0; g < fwi_plan::kMaxGroups - 1; ++g) {
+    if (!p->side[g]) CK(cudaStreamCreateWithFlags(&p->side[g], cudaStreamNonBlocking));
+    if (!p->ev_join[g]) CK(cudaEventCreateWithFlags(&p->ev_join[g], cudaEventDisableTiming));
+  }
   if (!p->ev_fork) CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
-  if (!p->ev_join) CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
   set_attrs(p);
   CK(cudaGetLastError());
   return FWI_OK;
@@ -1237,20 +1249,15 @@ fwi_status gradient_impl(fwi_plan* p, const float* c, const float* weights, cons
     LAUNCHED("k_accumulate");
     return FWI_OK;
   };
-  const int G = (p->sched.stream_groups == 2 && K >= 2) ? 2 : 1;
-  const int KA = G == 2 ? (K + 1) / 2 : K;
-  if (G == 2) {
-    CK(cudaEventRecord(p->ev_fork, st));
-    CK(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
-  }
+  const int G = group_count(p, K), KG = (K + G - 1) / G;
+  if ((s = fork_groups(p, G, st)) != FWI_OK) return s;
   for (int it = 0; it < nit; ++it) {
-    if ((s = iterate(it, 0, KA, st)) != FWI_OK) return s;
-    if (G == 2 && (s = iterate(it, KA, K - KA, p->side)) != FWI_OK) return s;
+    for (int g = 0; g < G; ++g) {
+      const int k0 = g * KG, nk = std::min(K, k0 + KG) - k0;
+      if (nk > 0 && (s = iterate(it, k0, nk, group_stream(p, g, st))) != FWI_OK) return s;
+    }
   }
-  if (G == 2) {
-    CK(cudaEventRecord(p->ev_join, p->side));
-    CK(cudaStreamWaitEvent(st, p->ev_join, 0));
-  }
+  if ((s = join_groups(p, G, st)) != FWI_OK) return s;
   // mean over shots, scaled to dD/dc if requested
   const double scale = q.c_rec > 0 ? q.dx * q.c_rec / 2.0 : 1.0;
   CK(cudaMemsetAsync(grad, 0, (size_t)p->nvox * 8, st));
@@ -1488,7 +1495,7 @@ fwi_status fwi_plan_set_schedule(fwi_plan* p, const fwi_schedule* sc) {
   if (!p || !sc) return FWI_EINVAL;
   if (sc->specialized < 0 || sc->specialized > 2 || sc->radix_order < 0 || sc->radix_order > 2 ||
       (sc->z_tile != 16 && sc->z_tile != 32) || (sc->split_plane != 0 && sc->split_plane != 1) ||
-      (sc->stream_groups != 1 && sc->stream_groups != 2))
+      (sc->stream_groups != 1 && sc->stream_groups != 2 && sc->stream_groups != 4))
     return FWI_EINVAL;
   const fwi_schedule old = p->sched;
   p->sched = *sc;
@@ -1510,9 +1517,11 @@ fwi_status fwi_plan_get_schedule(const fwi_plan* p, fwi_schedule* sc) {
 fwi_status fwi_plan_destroy(fwi_plan* p) {
   if (p) {
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
-    if (p->side) cudaStreamDestroy(p->side);
+    for (int g = 0; g < fwi_plan::kMaxGroups - 1; ++g) {
+      if (p->side[g]) cudaStreamDestroy(p->side[g]);
+      if (p->ev_join[g]) cudaEventDestroy(p->ev_join[g]);
+    }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
-    if (p->ev_join) cudaEventDestroy(p->ev_join);
   }
   delete p;
   return FWI_OK;
