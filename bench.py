@@ -428,10 +428,28 @@ def main():
     # time includes time shared with the other group's kernels)
     step_bpv = sum(alg_bytes_per_voxel(k, wl.nx) for k in fwi.KERNELS)
     step_gbs = step_bpv * vsteps * args.steps / (tot_ms / 1e3) / 1e9
+    # the same kernel in one untimed gradient with one stream group (all simulations of a
+    # phase in each launch, nothing overlapping it): the kernel's own efficiency
+    iso = None
+    if schedule.get("stream_groups", 1) > 1:
+        autotune.set_schedule(plan, dict(schedule, stream_groups=1))
+        plan.profile(dominant, enable=True)
+        step()
+        torch.cuda.synchronize(dev)
+        plan.profile(dominant, enable=False)
+        i_ms, i_launches, i_sims = plan.profile_read()[dominant]
+        autotune.set_schedule(plan, schedule)
+        i_ach = bpv * wl.n_vox * i_sims / (i_ms / 1e3) / 1e9
+        iso = {"achieved": i_ach, "frac": i_ach / hbm, "avg_launch_ms": i_ms / max(i_launches, 1),
+               "sims_per_launch": i_sims / max(i_launches, 1), "stream_groups": 1}
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm,
                 "peak_kind": kind, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
                 "traffic": None, "alg_bytes_per_voxel": bpv,
                 "step": {"alg_bytes_per_voxel_step": step_bpv, "achieved": step_gbs, "frac": step_gbs / hbm},
+                "isolated": iso,
+                "note": ("achieved/frac: the kernel's CUDA-event time over the timed region, where its "
+                         "launches overlap the other stream groups' kernels; isolated: the same kernel "
+                         "with one stream group; step: all kernels' algorithmic bytes over the step time"),
                 "avg_launch_ms": kern_ms / max(kern_launches, 1), "launches_timed": kern_launches,
                 "kernel_share_of_step": {k: v / sum(share_ms.values()) for k, v in share_ms.items()}}
 
@@ -439,7 +457,7 @@ def main():
     plain = None
     if args.plain_steps > 0:
         pplan = fwi.Plan.from_workload(wl, pairing="literal", max_shots=K, sims_per_launch=1, device=dev)
-        autotune.set_schedule(pplan, schedule)
+        autotune.set_schedule(pplan, dict(schedule, stream_groups=1))   # sequential simulations
         pplan.gradient(c_model, w, observed, misfit=misfit, grad=grad)
         torch.cuda.synchronize(dev)
         pt = []
@@ -454,7 +472,8 @@ def main():
         pms = sum(pt) / len(pt)
         plain = {"value": vsteps / (pms / 1e3) / 1e9, "unit": UNIT,
                  "gradients_per_h": 3600.0 / (pms / 1e3), "ms_per_step": pms,
-                 "form": "one simulation per launch sequence (sims_per_launch = 1)"}
+                 "form": "one simulation per launch sequence, simulations one after another "
+                         "(sims_per_launch = 1, one stream group)"}
         pplan.close()
         del pplan
 
