@@ -313,10 +313,13 @@ def main():
     ap.add_argument("--requests", type=int, default=64, help="serve: length of the request stream")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--inflight", type=int, default=8, help="serve: admitted requests at most")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve"],
+    ap.add_argument("--level", type=int, default=2, help="level: serving grid (0, 1, 2)")
+    ap.add_argument("--pz", type=int, default=0, help="level: physical z extent override (profiling)")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve", "level"],
                     help="plain: the 128x128x64 gradient (the reported line); batch: the 16-instance "
                          "uneven-grid configuration as one captured graph vs sequential forms; "
-                         "serve: the Poisson request stream over the three multigrid levels")
+                         "serve: the Poisson request stream over the three multigrid levels; "
+                         "level: one gradient (one super-shot) on a serving grid")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -342,10 +345,16 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    wl = synth.config2()
+    if args.workload == "level":
+        wl = synth.serving_level(args.level, n_src=8, seed=1000 + args.level, pz=args.pz or None)
+    else:
+        wl = synth.config2()
     if args.nt:
         wl.nt = args.nt
         wl.wavelet = wl.wavelet[:args.nt]
+    workload = WORKLOAD if args.workload != "level" else (
+        f"serving level {args.level}: one TR gradient (one super-shot of 8 emitters, 1024 receivers) "
+        f"on the {wl.nx}x{wl.ny}x{wl.nz} grid, {wl.nt} steps")
     K = wl.weights.shape[0]
     if rank > 0:   # independent estimates per GPU (Sec. 4.5): other encoding weights
         rng = np.random.default_rng(1000 + rank)
@@ -520,7 +529,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [wl.nx, wl.ny, wl.nz], "nt": wl.nt,
+        "config": {"workload": workload, "grid": [wl.nx, wl.ny, wl.nz], "nt": wl.nt,
                    "super_shots": K, "n_src": int(len(wl.src_idx)), "n_rec": int(len(wl.rec_idx)),
                    "n_gamma": int(len(wl.gamma_idx)), "n_layer": int(len(wl.layer_idx)),
                    "pairing": "literal", "voxel_steps_per_step": vsteps, "fft_schedule": schedule,

@@ -298,9 +298,19 @@ __device__ __forceinline__ void p2_yfwd_a(const float2* in, float2* out, const f
   }
 }
 
+// Old field values come from the staged rows in shared memory, or (GIN) from global memory,
+// where each element is read once by the thread that later overwrites it and by no other
+// thread: a read-only (non-coherent) load is then safe, and it lets the loads of all k2 be
+// issued before the stores instead of one round trip after another.
+template <bool GIN>
+__device__ __forceinline__ float old_value(const float* p) {
+  if constexpr (GIN) return __ldg(p);
+  else return *p;
+}
+
 // phase 4, momentum: derivative of both rows in registers, v_comp update in place
 // (Lambda^s (Lambda^s v - dt/rho0 d+ p)), then forward x step A of the new v -> out
-template <class G>
+template <class G, bool GIN>
 __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, const float2* twxT,
                                               float* __restrict__ v, const float* vin, int rs,
                                               const float* __restrict__ lam, int comp, float lz, float dtr,
@@ -321,8 +331,8 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
     if constexpr (PRE) {
       sfor<0, G::AX2>([&](auto K2) {
         constexpr int k2 = decltype(K2)::value;
-        s0[k2] = i0[G::AX1 * k2];
-        s1[k2] = has1 ? i1[G::AX1 * k2] : 0.f;
+        s0[k2] = old_value<GIN>(&i0[G::AX1 * k2]);
+        s1[k2] = has1 ? old_value<GIN>(&i1[G::AX1 * k2]) : 0.f;
       });
     }
     float2 z[G::AX2];
@@ -340,7 +350,7 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
       if (comp == 0) a0 = a1 = __ldg(&lam[k1 + G::AX1 * k2]);
       float o0v, o1v;
       if constexpr (PRE) { o0v = s0[k2]; o1v = s1[k2]; }
-      else { o0v = i0[G::AX1 * k2]; o1v = has1 ? i1[G::AX1 * k2] : 0.f; }
+      else { o0v = old_value<GIN>(&i0[G::AX1 * k2]); o1v = has1 ? old_value<GIN>(&i1[G::AX1 * k2]) : 0.f; }
       const float n0 = a0 * (a0 * o0v - dtr * z[k2].x);
       v0p[G::AX1 * k2] = n0;
       float n1 = 0.f;
@@ -356,11 +366,12 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
 
 // phase 4, mass: rho_comp <- Lambda (Lambda rho - dt rho0 d- v); for the last
 // component also p = c0^2 (rho_x + rho_y + rho_z), written as pairs to pout.
-template <class G, bool LAST>
+template <class G, bool LAST, bool GIN>
 __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, float* __restrict__ rho,
                                                const float* rin, int rs, const float* __restrict__ lam,
-                                               int comp, float lz, float dtr0, const float* rx,
-                                               const float* rz, const float* __restrict__ c2, int nyl) {
+                                               int comp, float lz, float dtr0, const float* __restrict__ rx,
+                                               const float* __restrict__ rz, const float* __restrict__ c2,
+                                               int nyl) {
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
     const int p = t / G::AX1, k1 = t - p * G::AX1;
     const int y0 = 2 * p, y1 = y0 + 1;
@@ -374,8 +385,8 @@ __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, fl
     if constexpr (PRE) {
       sfor<0, G::AX2>([&](auto K2) {
         constexpr int k2 = decltype(K2)::value;
-        s0[k2] = i0[G::AX1 * k2];
-        s1[k2] = has1 ? i1[G::AX1 * k2] : 0.f;
+        s0[k2] = old_value<GIN>(&i0[G::AX1 * k2]);
+        s1[k2] = has1 ? old_value<GIN>(&i1[G::AX1 * k2]) : 0.f;
       });
     }
     float2 z[G::AX2];
@@ -395,7 +406,7 @@ __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, fl
       if (comp == 0) a0 = a1 = __ldg(&lam[k1 + xo]);
       float o0v, o1v;
       if constexpr (PRE) { o0v = s0[k2]; o1v = s1[k2]; }
-      else { o0v = i0[xo]; o1v = has1 ? i1[xo] : 0.f; }
+      else { o0v = old_value<GIN>(&i0[xo]); o1v = has1 ? old_value<GIN>(&i1[xo]) : 0.f; }
       const float r0 = a0 * (a0 * o0v - dtr0 * z[k2].x);
       rho[o0 + xo] = r0;
       float r1 = 0.f;
@@ -456,7 +467,7 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mom(const __gr
     if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
     constexpr bool SS = G::STAGE && P2_STAGE_STATE;
-    p2_mom_update<G>(S, X, twxT, vg, SS ? reinterpret_cast<const float*>(Gb) : vg, SS ? G::RS : NX,
+    p2_mom_update<G, !SS>(S, X, twxT, vg, SS ? reinterpret_cast<const float*>(Gb) : vg, SS ? G::RS : NX,
                      P.lams[comp], comp, lz, P.dt_over_rho0, NY);
     __syncthreads();
     if constexpr (G::STAGE) {                               // next spectrum overlaps phases 5-7
@@ -512,11 +523,11 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
     const int rs = SS ? G::RS : NX;
     if (cc < 2) {
       p2_fetch_spec<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff);   // overlaps phase 4
-      p2_mass_update<G, false>(S, nullptr, rg, rin, rs, P.lam[comp], comp, lz, P.dt_rho0, nullptr, nullptr,
-                               nullptr, NY);
+      p2_mass_update<G, false, !SS>(S, nullptr, rg, rin, rs, P.lam[comp], comp, lz, P.dt_rho0, nullptr,
+                                    nullptr, nullptr, NY);
     } else {
-      p2_mass_update<G, true>(S, X, rg, rin, rs, P.lam[1], 1, lz, P.dt_rho0, Q.rho[0] + voff,
-                              Q.rho[2] + voff, P.c2 + voff, NY);
+      p2_mass_update<G, true, !SS>(S, X, rg, rin, rs, P.lam[1], 1, lz, P.dt_rho0, Q.rho[0] + voff,
+                                   Q.rho[2] + voff, P.c2 + voff, NY);
     }
   }
   __syncthreads();

@@ -20,10 +20,12 @@ struct Y2 {
   static constexpr int NT = TY * N2;
   static_assert(N1 <= N2, "step B runs on the first TY * N1 threads");
   static constexpr size_t SMEM = (size_t)(NY + NY * TY) * 8;
+  // two CTAs per SM where the register budget allows it without spilling the step-B lines
+  static constexpr int MINB = N2 <= 24 && NY > 256 ? 2 : 1;
 };
 
 template <int KIND, int NY, int TY>
-__global__ void __launch_bounds__(Y2<NY, TY>::NT) k_ypass2(const __grid_constant__ StepParams P) {
+__global__ void __launch_bounds__(Y2<NY, TY>::NT, Y2<NY, TY>::MINB) k_ypass2(const __grid_constant__ StepParams P) {
   using C = Y2<NY, TY>;
   constexpr int N1 = C::N1, N2 = C::N2;
   constexpr bool INV = KIND == Y_INV_MOM || KIND == Y_INV_MASS;
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mom(const __grid_
     x2_xinv_a<G>(X, S, twx, comp == 0 ? P.ap[0] : nullptr, nyl);
     __syncthreads();
     float* v = Q.v[comp] + voff;
-    p2_mom_update<G>(S, X, twxT, v, v, NX, comp == 1 ? P.lams[1] + 2 * p0 : P.lams[comp], comp, lz,
+    p2_mom_update<G, true>(S, X, twxT, v, v, NX, comp == 1 ? P.lams[1] + 2 * p0 : P.lams[comp], comp, lz,
                      P.dt_over_rho0, nyl);
     __syncthreads();
     p2_xfwd_b<G>(X, S);
@@ -255,10 +257,11 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mass(const __grid
     const float* lam = comp == 1 ? P.lam[1] + 2 * p0 : P.lam[comp];
     if (cc < 2) {
       x2_load_rows<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff, p0, ny);   // overlaps the update
-      p2_mass_update<G, false>(S, nullptr, rg, rg, NX, lam, comp, lz, P.dt_rho0, nullptr, nullptr, nullptr, nyl);
+      p2_mass_update<G, false, true>(S, nullptr, rg, rg, NX, lam, comp, lz, P.dt_rho0, nullptr, nullptr, nullptr,
+                                     nyl);
     } else {
-      p2_mass_update<G, true>(S, X, rg, rg, NX, lam, comp, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
-                              P.c2 + voff, nyl);
+      p2_mass_update<G, true, true>(S, X, rg, rg, NX, lam, comp, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
+                                    P.c2 + voff, nyl);
     }
   }
   __syncthreads();

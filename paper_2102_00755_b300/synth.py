@@ -310,18 +310,20 @@ SERVING_LEVELS = {
 }
 
 
-def serving_level(level: int, n_src: int, seed: int, n_rec: int = 1024) -> Workload:
+def serving_level(level: int, n_src: int, seed: int, n_rec: int = 1024, pz: int = None) -> Workload:
     """A multigrid level of the serving stream: physical grid padded by the PML
-    size rule, Ricker frequency scaled with dx (1 MHz at 0.5 mm)."""
-    (px, py, pz), dx, nt = SERVING_LEVELS[level]
+    size rule, Ricker frequency scaled with dx (1 MHz at 0.5 mm).  `pz` replaces the
+    physical z extent (a thinner grid with the same planes, for profiling)."""
+    (px, py, pz0), dx, nt = SERVING_LEVELS[level]
+    pz = pz0 if pz is None else pz
     P = [optimal_pml(n) for n in (px, py, pz)]
     nx, ny, nz = px + 2 * P[0], py + 2 * P[1], pz + 2 * P[2]
     shp = (nx, ny, nz)
     dt = time_step(dx)
     rng = np.random.default_rng(seed)
     # breast in the physical region, bowl radius 0.473 of the physical width
-    R = 0.473 * px
     z_e = P[2] + pz - 2
+    R = min(0.473 * px, z_e - 1.0)       # the bowl must fit the grid when z is overridden
     centre = (nx / 2.0, ny / 2.0, float(z_e))
     semi = (0.7 * 0.7 * R, 0.7 * 0.7 * R, 0.8 * 0.7 * R)
     gamma = half_ellipsoid_mask(shp, centre, semi)
