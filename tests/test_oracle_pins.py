@@ -591,3 +591,55 @@ def test_slbfgs_projection_and_averaging():
     idx = range(first + 1, len(us))
     w = np.array([(i + 1) ** 3 for i in idx], dtype=float)
     assert np.allclose(u_hat, sum(wi * us[i] for wi, i in zip(w, idx)) / w.sum())
+
+
+# ---------------------------------------------------------------------------
+# Grid transfers of the coarse-to-fine scheme (Sec. 3.3, App. C)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_in,n_out,kind", [(11, 21, "blackman"), (21, 11, "kaiser"), (16, 33, "none"),
+                                              (24, 16, "none"), (9, 9, "blackman")])
+def test_resampling_matches_trigonometric_sum(n_in, n_out, kind):
+    """The FFT evaluation equals the brute-force windowed trigonometric sum."""
+    from oracle import multigrid
+    u = np.random.default_rng(n_in * 31 + n_out).standard_normal(n_in)
+    fast = multigrid.resample_1d(u, n_out, 0, kind)
+    slow = multigrid.trig_sum(u, n_out, kind)
+    assert np.allclose(fast, slow, rtol=1e-12, atol=1e-12)
+
+
+def test_fourier_interpolation_is_exact_for_band_limited_signals():
+    """Rectangular window: a trigonometric polynomial inside the band is reproduced exactly
+    at the fine sample positions, in 3D and for odd and even sizes."""
+    from oracle import multigrid
+    def f(shape, scale):
+        z, y, x = np.meshgrid(*[np.arange(n) * scale[a] for a, n in enumerate(shape)], indexing="ij")
+        return (1.0 + np.cos(2 * np.pi * 2 * x / shape[2] / scale[2]) * np.sin(2 * np.pi * 1 * y / shape[1] / scale[1])
+                + 0.5 * np.cos(2 * np.pi * 3 * z / shape[0] / scale[0] + 0.3))
+    shape_c, shape_f = (9, 12, 11), (17, 24, 21)
+    uc = f(shape_c, (1.0, 1.0, 1.0))
+    uf = f(shape_f, tuple(c / n for c, n in zip(shape_c, shape_f)))
+    assert np.allclose(multigrid.resample(uc, shape_f, "none"), uf, atol=1e-12)
+
+
+def test_windows_dc_gain_and_attenuation():
+    """DC is kept (w(0) = 1), a pure cosine of band index k comes out scaled by w(k),
+    and a component beyond the coarse band is removed by down-sampling."""
+    from oracle import multigrid
+    n = 40
+    t = np.arange(n)
+    for kind in ("blackman", "kaiser"):
+        K = multigrid.band(n, 80)
+        w = multigrid.window(kind, K)
+        assert abs(w[0] - 1.0) < 1e-15
+        k = 5
+        out = multigrid.resample_1d(3.0 + np.cos(2 * np.pi * k * t / n), 80, 0, kind)
+        ref = 3.0 + w[k] * np.cos(2 * np.pi * k * np.arange(80) / 80)
+        assert np.allclose(out, ref, atol=1e-12)
+    hi = np.cos(2 * np.pi * 15 * t / n)            # above the band of a 20-sample output
+    assert np.abs(multigrid.downsample_series(hi, 20, 0)).max() < 1e-12
+
+
+def test_data_scaling_eta():
+    from oracle import multigrid
+    x = np.ones(30)
+    assert np.allclose(multigrid.downsample_series(x, 15, 0, eta=2.0), 4.0)
