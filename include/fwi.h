@@ -204,6 +204,34 @@ fwi_status fwi_grad_to_param(int64_t n, int32_t kind, const float *c, const doub
                              void *stream);
 
 /*
+ * Grid transfers of the coarse-to-fine scheme (Sec. 3.3, App. C): separable periodic
+ * Fourier resampling of a real array [n2][n1][n0] (axis 0 fastest) to [m2][m1][m0].
+ * Along each axis a the output sample i is the windowed trigonometric interpolant of
+ * the input at t = i n_a / m_a over the band |k| <= K = floor((min(n_a, m_a) - 1) / 2):
+ *   out_i = (1/n_a) sum_j in_j (w(0) + 2 sum_{k=1..K} w(k) cos(2 pi k (t - j) / n_a)),
+ * window[a]: 0 = none (plain Fourier interpolation), 1 = Blackman (model up-sampling),
+ * 2 = Kaiser with parameter kaiser_beta (time-series low-pass); both windows are 1 at
+ * k = 0 and vanish just beyond the band.  Axes with n_a = m_a and window 0 are left as
+ * they are.  The output is multiplied by `scale` (eta^(d-1) for data down-sampled in time,
+ * App. C; 1 otherwise; it needs at least one resampled axis).  FP32 arrays, FP64
+ * accumulation.
+ *   fwi_resampler_create: host; reports the workspace size (matrices + two intermediates).
+ *   fwi_resampler_bind_workspace: caller-owned device memory, 256-byte aligned; uploads
+ *                         the matrices (synchronous).
+ *   fwi_resample:         in (device [n2][n1][n0]) -> out (device [m2][m1][m0]); in and
+ *                         out must not overlap.  Asynchronous on `stream`.
+ * Errors: FWI_EINVAL (NULL, sizes outside 1..8192, bad window, beta < 0, unbound),
+ * FWI_ENOMEM, FWI_ECUDA.
+ */
+typedef struct fwi_resampler fwi_resampler;
+fwi_status fwi_resampler_create(const int32_t n_in[3], const int32_t n_out[3], const int32_t window[3],
+                                double kaiser_beta, double scale, size_t *workspace_bytes,
+                                fwi_resampler **out);
+fwi_status fwi_resampler_bind_workspace(fwi_resampler *resampler, void *dev_ptr, size_t bytes);
+fwi_status fwi_resample(fwi_resampler *resampler, const float *in, float *out, void *stream);
+fwi_status fwi_resampler_destroy(fwi_resampler *resampler);
+
+/*
  * Wait for the plan's last call and report its device-side status:
  * FWI_EUNSTABLE if its sound speed was outside (0, c_ref] (the call's outputs are
  * then undefined), FWI_ECUDA on an asynchronous CUDA error, else FWI_OK.

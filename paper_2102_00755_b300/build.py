@@ -8,7 +8,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfwi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared"]
-SOURCES = ["fwi.cu", "lbfgs.cu"]
+SOURCES = ["fwi.cu", "lbfgs.cu", "resample.cu"]
 
 
 def _sources_newer(target):

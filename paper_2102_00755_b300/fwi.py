@@ -36,7 +36,8 @@ C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_g
              "fwi_batch_gradient", "fwi_batch_nodes", "fwi_batch_destroy", "fwi_plan_destroy",
              "fwi_status_string", "fwi_last_cuda_error", "fwi_lbfgs_create", "fwi_lbfgs_bind_workspace",
              "fwi_lbfgs_push", "fwi_lbfgs_apply", "fwi_lbfgs_size", "fwi_lbfgs_destroy", "fwi_vec_step_project",
-             "fwi_vec_accumulate", "fwi_param_to_speed", "fwi_grad_to_param")
+             "fwi_vec_accumulate", "fwi_param_to_speed", "fwi_grad_to_param", "fwi_resampler_create",
+             "fwi_resampler_bind_workspace", "fwi_resample", "fwi_resampler_destroy")
 
 NOALLOC_MAX_PARTIALS = 8192
 
@@ -150,6 +151,16 @@ def lib():
         L.fwi_param_to_speed.restype = ctypes.c_int
         L.fwi_grad_to_param.argtypes = [i64, i32, vp, vp, vp, vp]
         L.fwi_grad_to_param.restype = ctypes.c_int
+        i32x3 = ctypes.c_int32 * 3
+        L.fwi_resampler_create.argtypes = [i32x3, i32x3, i32x3, dbl, dbl, ctypes.POINTER(ctypes.c_size_t),
+                                           ctypes.POINTER(vp)]
+        L.fwi_resampler_create.restype = ctypes.c_int
+        L.fwi_resampler_bind_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+        L.fwi_resampler_bind_workspace.restype = ctypes.c_int
+        L.fwi_resample.argtypes = [vp, vp, vp, vp]
+        L.fwi_resample.restype = ctypes.c_int
+        L.fwi_resampler_destroy.argtypes = [vp]
+        L.fwi_resampler_destroy.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -233,6 +244,27 @@ def fwi_param_to_speed(n, kind, u_ptr, c_ptr, stream) -> int:
 
 def fwi_grad_to_param(n, kind, c_ptr, gc_ptr, gu_ptr, stream) -> int:
     return lib().fwi_grad_to_param(n, kind, c_ptr, gc_ptr, gu_ptr, stream)
+
+
+def fwi_resampler_create(n_in, n_out, window, beta, scale=1.0):
+    ws = ctypes.c_size_t(0)
+    h = ctypes.c_void_p(0)
+    a = ctypes.c_int32 * 3
+    st = lib().fwi_resampler_create(a(*n_in), a(*n_out), a(*window), float(beta), float(scale), ctypes.byref(ws),
+                                    ctypes.byref(h))
+    return st, h, ws.value
+
+
+def fwi_resampler_bind_workspace(h, ptr: int, nbytes: int) -> int:
+    return lib().fwi_resampler_bind_workspace(h, ctypes.c_void_p(ptr), nbytes)
+
+
+def fwi_resample(h, in_ptr, out_ptr, stream) -> int:
+    return lib().fwi_resample(h, in_ptr, out_ptr, stream)
+
+
+def fwi_resampler_destroy(h) -> int:
+    return lib().fwi_resampler_destroy(h)
 
 
 def fwi_plan_status(plan) -> int:
