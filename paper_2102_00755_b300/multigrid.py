@@ -80,3 +80,40 @@ def embed_physical(c_phys: torch.Tensor, shape, pml, fill: float) -> torch.Tenso
     out = torch.full(shape, fill, dtype=torch.float32, device=c_phys.device)
     out[pz:shape[0] - pz, py:shape[1] - py, px:shape[2] - px] = c_phys
     return out
+
+
+def coarse_to_fine(stages, n_evl, nu: float = 1.0, m: int = 8, h0_frac: float = 0.01, K: int = 1,
+                   param: str = "squared_slowness", c_min: float = 1350.0, c_max: float = 1800.0, seed0: int = 0):
+    """Coarse-to-fine inversion (Sec. 3.3): SLBFGS (Alg. 2) on each grid in turn, the
+    result transferred to the next grid by `upsample_model` on the physical region.
+
+    stages: list of (plan, raw observed data [n_src][nt][n_rec] on that grid, pml,
+            shape (nz, ny, nx)), coarse to fine, each plan with max_shots >= K; n_evl:
+            estimator evaluations per stage; K: super-shots per estimate.
+    Returns the final model [nz][ny][nx] and the energy estimates of every stage.
+    The initial model of the first stage is water.  h0 is chosen per stage so that the
+    first step changes the parameter by about h0_frac of its norm.
+    """
+    from . import slbfgs
+    from .synth import C_WATER
+    kind = slbfgs.PARAM_KINDS[param]
+    to_u = {0: lambda c: c, 1: lambda c: 1.0 / c, 2: lambda c: 1.0 / (c * c)}[kind]
+    u_lo, u_hi = sorted((to_u(c_min), to_u(c_max)))
+    c = None
+    energies = []
+    for plan, raw, pml, shape in stages:
+        if c is None:
+            c = torch.full(shape, C_WATER, dtype=torch.float32, device=raw.device)
+        else:
+            phys = upsample_model(physical(c, prev_pml), (shape[0] - 2 * pml[2], shape[1] - 2 * pml[1],
+                                                          shape[2] - 2 * pml[0]))
+            c = embed_physical(phys, shape, pml, C_WATER)
+        est = slbfgs.FwiEstimator(plan, raw, K=K, param=param, seed0=seed0)
+        u0 = to_u(c.reshape(-1).to(torch.float64))
+        _, g0 = est(u0, 0.0, 0)
+        h0 = h0_frac * float(u0.norm()) / max(float(g0.norm()), 1e-300)
+        u, Js = slbfgs.SLBFGS(est, nu=nu, m=m, h0=h0, u_min=u_lo, u_max=u_hi).run(u0, n_evl)
+        c = est.speed(u.contiguous()).clone().reshape(shape)
+        energies.append(Js)
+        prev_pml = pml
+    return c, energies
