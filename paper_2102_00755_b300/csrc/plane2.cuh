@@ -32,6 +32,16 @@
 
 namespace fwi {
 
+#ifndef P2_TW_POW
+#define P2_TW_POW 1
+#endif
+#ifndef P2_REMAP
+#define P2_REMAP 1
+#endif
+#ifndef P2_MERGE
+#define P2_MERGE 1
+#endif
+
 __host__ __device__ constexpr int cmax3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
 
 template <int NX, int NY>
@@ -53,10 +63,21 @@ struct Plane2 {
   static constexpr int NT = NX == 128 ? 544 : NX == 135 ? 352 : NX == 160 ? 416 : NX == 96 ? 416
                           : NX == 64 ? 288 : 128;
   static constexpr int TW = NX + NX + NY;                 // twx, twxT, twy
+  // Phase-4 task order.  Tasks (p, k1) of one half-warp read and write 64-bit words at
+  // p PST + k1 + const in S and X; with AX1 = 8 and PST = PA = 1 (mod 16) the row pairs
+  // p and p + 1 would share seven of their eight banks.  REMAP pairs p with p + 8
+  // instead (PST 8 = 8 mod 16: disjoint banks); the warp's four row pairs are then
+  // p, p + 8, p + 1, p + 9.
+  static constexpr bool REMAP = P2_REMAP && AX1 == 8 && AX2 % 16 == 0 && PST % 16 == 1 && NP % 16 == 0;
   // staging buffer (complex units) for the next global input: a spectrum plane, or a
-  // real field plane with rows padded to NX + 4 floats (conflict-free phase-4 reads)
-  static constexpr int RS = NX + 4;
-  static constexpr int GS = (HX * NY > (NY * RS + 1) / 2) ? HX * NY : (NY * RS + 1) / 2;
+  // real field plane with padded rows.  Row y starts at row_off(y) floats (a multiple of
+  // 4: 16-byte copies).  The phase-4 reads of one warp take 8 floats from each of the
+  // rows 2p of its four row pairs: rows NX + 4 long make p = 0..3 (the order without
+  // REMAP) hit the bank windows 0, 8, 16, 24; with REMAP, rows NX + 8 long plus 8 floats
+  // on every other block of 16 rows do the same for p, p + 8, p + 1, p + 9.
+  static constexpr int RS = REMAP ? NX + 8 : NX + 4;
+  __host__ __device__ static constexpr int row_off(int y) { return y * RS + (REMAP ? 8 * ((y >> 4) & 1) : 0); }
+  static constexpr int GS = (HX * NY > (row_off(NY - 1) + NX + 1) / 2) ? HX * NY : (row_off(NY - 1) + NX + 1) / 2;
   static constexpr int TWP = (TW + 1) & ~1;              // keeps the buffers 16-byte aligned
   static constexpr size_t SMEM_NOSTAGE = (size_t)(TWP + 2 * NP * PST) * 8;
   static constexpr bool STAGE = SMEM_NOSTAGE + (size_t)GS * 8 <= 227 * 1024 && (HX * NY) % 2 == 0;
@@ -86,14 +107,11 @@ __device__ __forceinline__ void p2_fetch_rows(float2* Gb, const float* __restric
   float* d = reinterpret_cast<float*>(Gb);
   for (int i = threadIdx.x; i < G::NYc * per_row; i += G::NT) {
     const int y = i / per_row, c = i - y * per_row;
-    cp_async16(d + y * G::RS + 4 * c, src + y * G::NXc + 4 * c);
+    cp_async16(d + G::row_off(y) + 4 * c, src + y * G::NXc + 4 * c);
   }
   cp_async_commit();
 }
 
-#ifndef P2_TW_POW
-#define P2_TW_POW 1
-#endif
 #ifndef P2_STAGE_STATE
 #define P2_STAGE_STATE 1
 #endif
@@ -117,6 +135,15 @@ __device__ __forceinline__ void tw_row(const float2* tab, int stride, float2 (&w
 template <class G>
 __device__ __forceinline__ float2* p2_row(float2* buf, int ky) {
   return buf + (ky >> 1) * G::PST + (ky & 1) * G::HX;
+}
+
+// phase-4 task t -> row pair p and column k1 (see Plane2::REMAP)
+template <class G>
+__device__ __forceinline__ void p2_task4(int t, int& p, int& k1) {
+  const int q = t / G::AX1;
+  k1 = t - q * G::AX1;
+  if constexpr (G::REMAP) p = (q & ~15) | ((q & 1) << 3) | ((q >> 1) & 7);
+  else p = q;
 }
 
 // twiddles: twx[e] = W_NX^e, twxT[k1' AX1 + j2'] = W_NX^(j2' k1'), twy[e] = W_NY^e
@@ -312,18 +339,20 @@ __device__ __forceinline__ float old_value(const float* p) {
 // (Lambda^s (Lambda^s v - dt/rho0 d+ p)), then forward x step A of the new v -> out
 template <class G, bool GIN>
 __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, const float2* twxT,
-                                              float* __restrict__ v, const float* vin, int rs,
+                                              float* __restrict__ v, const float* vin,
                                               const float* __restrict__ lam, int comp, float lz, float dtr,
                                               int nyl) {
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
-    const int p = t / G::AX1, k1 = t - p * G::AX1;
+    int p, k1;
+    p2_task4<G>(t, p, k1);
     const int y0 = 2 * p, y1 = y0 + 1;
     if (y0 >= nyl) continue;
     const bool has1 = y1 < nyl;
     float* v0p = v + y0 * G::NXc + k1;
     float* v1p = v0p + G::NXc;
-    const float* i0 = vin + y0 * rs + k1;
-    const float* i1 = i0 + rs;
+    // old values: global rows, or staged rows (y0 even: rows y0 and y0 + 1 share a block of 16)
+    const float* i0 = vin + (GIN ? y0 * G::NXc : G::row_off(y0)) + k1;
+    const float* i1 = i0 + (GIN ? G::NXc : G::RS);
     // the old field is loaded ahead of the transform unless that would hold too many
     // registers (long step-B lines)
     constexpr bool PRE = G::AX2 <= 16;
@@ -368,18 +397,19 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
 // component also p = c0^2 (rho_x + rho_y + rho_z), written as pairs to pout.
 template <class G, bool LAST, bool GIN>
 __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, float* __restrict__ rho,
-                                               const float* rin, int rs, const float* __restrict__ lam,
+                                               const float* rin, const float* __restrict__ lam,
                                                int comp, float lz, float dtr0, const float* __restrict__ rx,
                                                const float* __restrict__ rz, const float* __restrict__ c2,
                                                int nyl) {
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
-    const int p = t / G::AX1, k1 = t - p * G::AX1;
+    int p, k1;
+    p2_task4<G>(t, p, k1);
     const int y0 = 2 * p, y1 = y0 + 1;
     if (y0 >= nyl) continue;
     const bool has1 = y1 < nyl;
     const int o0 = y0 * G::NXc + k1, o1 = o0 + G::NXc;
-    const float* i0 = rin + y0 * rs + k1;
-    const float* i1 = i0 + rs;
+    const float* i0 = rin + (GIN ? y0 * G::NXc : G::row_off(y0)) + k1;
+    const float* i1 = i0 + (GIN ? G::NXc : G::RS);
     constexpr bool PRE = G::AX2 <= 16;   // as in the momentum update
     float s0[PRE ? G::AX2 : 1], s1[PRE ? G::AX2 : 1];
     if constexpr (PRE) {
@@ -448,17 +478,28 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mom(const __gr
   const size_t voff = (size_t)z * (NX * NY);
   // component order z, x, y: R -> V_z (spec[1]), Q -> V_x (spec[2]), Q -> V_y (spec[0])
   auto src_of = [&](int comp) { return (comp == 2 ? Q.spec[1] : Q.spec[0]) + soff; };
+  auto comp_of = [](int cc) { return cc == 0 ? 2 : cc - 1; };
+  auto phase1 = [&](int comp) {
+    p2_yinv_a<G>(S, G::STAGE ? Gb : src_of(comp), comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.ap[comp], twy);
+  };
   if constexpr (G::STAGE) p2_fetch_spec<G>(Gb, src_of(2));
   p2_stage_twiddles<G>(sm2, P);
   const float lz = __ldg(&P.lams[2][z]);
-#pragma unroll 1
-  for (int cc = 0; cc < 3; ++cc) {
-    const int comp = cc == 0 ? 2 : cc - 1;
-    float2* dst = (comp == 2 ? Q.spec[1] : (comp == 0 ? Q.spec[2] : Q.spec[0])) + soff;
-    float* vg = Q.v[comp] + voff;
+  if constexpr (P2_MERGE) {
     if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
-    p2_yinv_a<G>(S, G::STAGE ? Gb : src_of(comp), comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.ap[comp], twy);
+    phase1(comp_of(0));
+  }
+#pragma unroll 1
+  for (int cc = 0; cc < 3; ++cc) {
+    const int comp = comp_of(cc);
+    float2* dst = (comp == 2 ? Q.spec[1] : (comp == 0 ? Q.spec[2] : Q.spec[0])) + soff;
+    float* vg = Q.v[comp] + voff;
+    if constexpr (!P2_MERGE) {
+      if constexpr (G::STAGE) cp_async_wait_all();
+      __syncthreads();
+      phase1(comp);
+    }
     __syncthreads();
     if constexpr (G::STAGE && P2_STAGE_STATE) p2_fetch_rows<G>(Gb, vg);      // overlaps phases 2 and 3
     p2_y_b<G, true>(S, X, nullptr);
@@ -467,17 +508,23 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mom(const __gr
     if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
     constexpr bool SS = G::STAGE && P2_STAGE_STATE;
-    p2_mom_update<G, !SS>(S, X, twxT, vg, SS ? reinterpret_cast<const float*>(Gb) : vg, SS ? G::RS : NX,
-                     P.lams[comp], comp, lz, P.dt_over_rho0, NY);
+    p2_mom_update<G, !SS>(S, X, twxT, vg, SS ? reinterpret_cast<const float*>(Gb) : vg, P.lams[comp], comp, lz,
+                          P.dt_over_rho0, NY);
     __syncthreads();
     if constexpr (G::STAGE) {                               // next spectrum overlaps phases 5-7
-      if (cc < 2) p2_fetch_spec<G>(Gb, src_of(cc == 0 ? 0 : 1));
+      if (cc < 2) p2_fetch_spec<G>(Gb, src_of(comp_of(cc + 1)));
     }
     p2_xfwd_b<G>(X, S);
     __syncthreads();
     p2_yfwd_a<G>(S, X, twy);
+    if constexpr (P2_MERGE && G::STAGE) cp_async_wait_all();
     __syncthreads();
     p2_y_b<G, false>(X, nullptr, dst);
+    // with P2_MERGE, phase 1 of the next component shares this interval: it writes S
+    // (last read by phase 6) from the staged spectrum, phase 7 reads X
+    if constexpr (P2_MERGE) {
+      if (cc < 2) phase1(comp_of(cc + 1));
+    }
   }
 }
 
@@ -520,14 +567,13 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
     __syncthreads();
     constexpr bool SS = G::STAGE && P2_STAGE_STATE;
     const float* rin = SS ? reinterpret_cast<const float*>(Gb) : rg;
-    const int rs = SS ? G::RS : NX;
     if (cc < 2) {
       p2_fetch_spec<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff);   // overlaps phase 4
-      p2_mass_update<G, false, !SS>(S, nullptr, rg, rin, rs, P.lam[comp], comp, lz, P.dt_rho0, nullptr,
-                                    nullptr, nullptr, NY);
+      p2_mass_update<G, false, !SS>(S, nullptr, rg, rin, P.lam[comp], comp, lz, P.dt_rho0, nullptr, nullptr,
+                                    nullptr, NY);
     } else {
-      p2_mass_update<G, true, !SS>(S, X, rg, rin, rs, P.lam[1], 1, lz, P.dt_rho0, Q.rho[0] + voff,
-                                   Q.rho[2] + voff, P.c2 + voff, NY);
+      p2_mass_update<G, true, !SS>(S, X, rg, rin, P.lam[1], 1, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
+                                   P.c2 + voff, NY);
     }
   }
   __syncthreads();
@@ -583,7 +629,8 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
   __syncthreads();
   // forward x step A of p (pairs in X) -> S, then step B, R2C unpacking and y
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
-    const int p = t / G::AX1, k1 = t - p * G::AX1;
+    int p, k1;
+    p2_task4<G>(t, p, k1);
     const float2* r = X + p * G::PST + k1;
     float2 zz[G::AX2];
     sfor<0, G::AX2>([&](auto K2) { zz[decltype(K2)::value] = r[G::AX1 * decltype(K2)::value]; });

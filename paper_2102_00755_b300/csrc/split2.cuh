@@ -110,6 +110,10 @@ struct X2 {
   static constexpr int NT = ((T3 > T4 ? T3 : T4) + 31) / 32 * 32;
   static constexpr int TWP = (2 * NX + 1) & ~1;
   static constexpr size_t SMEM = (size_t)(TWP + 2 * NPC * PST) * 8;
+  // the shared update functions read old values from global rows here (no staging)
+  static constexpr bool REMAP = false;
+  static constexpr int RS = NX;
+  __host__ __device__ static constexpr int row_off(int y) { return y * NX; }
 };
 
 template <class G>
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mom(const __grid_
     x2_xinv_a<G>(X, S, twx, comp == 0 ? P.ap[0] : nullptr, nyl);
     __syncthreads();
     float* v = Q.v[comp] + voff;
-    p2_mom_update<G, true>(S, X, twxT, v, v, NX, comp == 1 ? P.lams[1] + 2 * p0 : P.lams[comp], comp, lz,
+    p2_mom_update<G, true>(S, X, twxT, v, v, comp == 1 ? P.lams[1] + 2 * p0 : P.lams[comp], comp, lz,
                      P.dt_over_rho0, nyl);
     __syncthreads();
     p2_xfwd_b<G>(X, S);
@@ -257,10 +261,10 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mass(const __grid
     const float* lam = comp == 1 ? P.lam[1] + 2 * p0 : P.lam[comp];
     if (cc < 2) {
       x2_load_rows<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff, p0, ny);   // overlaps the update
-      p2_mass_update<G, false, true>(S, nullptr, rg, rg, NX, lam, comp, lz, P.dt_rho0, nullptr, nullptr, nullptr,
+      p2_mass_update<G, false, true>(S, nullptr, rg, rg, lam, comp, lz, P.dt_rho0, nullptr, nullptr, nullptr,
                                      nyl);
     } else {
-      p2_mass_update<G, true, true>(S, X, rg, rg, NX, lam, comp, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
+      p2_mass_update<G, true, true>(S, X, rg, rg, lam, comp, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
                                     P.c2 + voff, nyl);
     }
   }
