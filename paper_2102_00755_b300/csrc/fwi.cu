@@ -467,7 +467,9 @@ fwi_status cuda_fail(cudaError_t e, const char* what) {
 // split planes: y-pass columns per CTA (8 where the 27-point step B needs the register
 // file of a smaller CTA) and x-pass row pairs per CTA
 __host__ __device__ constexpr int ty2_for(int n) { return n / split_n1(n) > 16 ? 8 : 16; }
-constexpr int kNPC2 = 8;
+// row pairs per CTA of the split x passes: 243 = 9 x 27 gives 9 update tasks per pair,
+// so 21 pairs (6 CTAs for the 122 pairs of a plane) keep the update phase's threads busy
+constexpr int npc2_for(int n) { return n == 243 ? 21 : 8; }
 #define S2_DISPATCH(p, CALL)                                            \
   switch ((p)->s2) {                                                    \
     case 243: { constexpr int N = 243; CALL; } break;                   \
@@ -522,8 +524,8 @@ void set_attrs_s2(int cap) {
   cudaFuncSetAttribute(k_ypass2<Y_INV_MASS, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_ypass2<Y_FWD3, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   cudaFuncSetAttribute(k_ypass2<Y_FWD1, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass2_mom<N, kNPC2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass2_mass<N, kNPC2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_xpass2_mom<N, npc2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  cudaFuncSetAttribute(k_xpass2_mass<N, npc2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }
 template <int NZ, int TZ>
 void set_attrs_z2(int cap) {
@@ -592,7 +594,8 @@ fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   const dim3 gx2((p->npair + warps * g2 - 1) / (warps * g2), p->prob.nz, P.nsims);
   const int ty2 = ty2_for(p->s2 > 0 ? p->s2 : 1);
   const dim3 gy2((p->hx + ty2 - 1) / ty2, p->prob.nz, P.nsims);
-  const dim3 gx2b((p->npair + kNPC2 - 1) / kNPC2, p->prob.nz, P.nsims);
+  const int npc2 = npc2_for(p->s2);
+  const dim3 gx2b((p->npair + npc2 - 1) / npc2, p->prob.nz, P.nsims);
   int slot;
   prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
   if (p->z2) {
@@ -607,7 +610,7 @@ fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   if (p->s2) {
     S2_DISPATCH(p, (k_ypass2<Y_INV_MOM, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
     LAUNCHED("k_ypass2<inverse, momentum>");
-    S2_DISPATCH(p, (k_xpass2_mom<N, kNPC2><<<gx2b, X2<N, kNPC2>::NT, p->smem_x2, st>>>(P)));
+    S2_DISPATCH(p, (k_xpass2_mom<N, npc2_for(N)><<<gx2b, X2<N, npc2_for(N)>::NT, p->smem_x2, st>>>(P)));
     LAUNCHED("k_xpass2_mom");
     S2_DISPATCH(p, (k_ypass2<Y_FWD3, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
     LAUNCHED("k_ypass2<forward x3>");
@@ -633,7 +636,7 @@ fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   if (p->s2) {
     S2_DISPATCH(p, (k_ypass2<Y_INV_MASS, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
     LAUNCHED("k_ypass2<inverse, mass>");
-    S2_DISPATCH(p, (k_xpass2_mass<N, kNPC2><<<gx2b, X2<N, kNPC2>::NT, p->smem_x2, st>>>(P)));
+    S2_DISPATCH(p, (k_xpass2_mass<N, npc2_for(N)><<<gx2b, X2<N, npc2_for(N)>::NT, p->smem_x2, st>>>(P)));
     LAUNCHED("k_xpass2_mass");
     S2_DISPATCH(p, (k_ypass2<Y_FWD1, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
     LAUNCHED("k_ypass2<forward x1>");
@@ -745,7 +748,7 @@ fwi_status apply_schedule(fwi_plan* p) {
     }
     if (p->split && q.nx == q.ny && in(q.nx, {243, 256, 480})) {
       p->s2 = q.nx;
-      S2_DISPATCH(p, (p->smem_y2 = Y2<N, ty2_for(N)>::SMEM, p->smem_x2 = X2<N, kNPC2>::SMEM));
+      S2_DISPATCH(p, (p->smem_y2 = Y2<N, ty2_for(N)>::SMEM, p->smem_x2 = X2<N, npc2_for(N)>::SMEM));
       if (p->smem_y2 > 227 * 1024 || p->smem_x2 > 227 * 1024) p->s2 = 0;
     }
     if (!p->p2 && !p->z2 && !p->s2) return FWI_ENOTSUP;

@@ -41,6 +41,9 @@ namespace fwi {
 #ifndef P2_MERGE
 #define P2_MERGE 1
 #endif
+#ifndef P2_NT128
+#define P2_NT128 640
+#endif
 
 __host__ __device__ constexpr int cmax3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
 
@@ -57,10 +60,10 @@ struct Plane2 {
   // task counts of the phases
   static constexpr int T1 = HX * BY2, T2 = HX * BY1, T3 = NP * AX2, T4 = NP * AX1;
   // Threads per CTA (one CTA per SM: the plane buffers take most of shared memory).
-  // Chosen per size so that the phases' task counts fill whole rounds of threads
-  // (e.g. 128: 1040, 520, 1024 and 512 tasks on 544 threads) while the kernels'
-  // registers still fit 64K per SM.
-  static constexpr int NT = NX == 128 ? 544 : NX == 135 ? 352 : NX == 160 ? 416 : NX == 96 ? 416
+  // Chosen per size by measurement, among counts whose registers fit 64K per SM; for
+  // 128 the phases' 1040, 520, 1024 and 512 tasks take 2, 1, 2 and 1 rounds of 640
+  // threads (544 fills the rounds better but hides less latency: 0.7 % slower).
+  static constexpr int NT = NX == 128 ? P2_NT128 : NX == 135 ? 352 : NX == 160 ? 416 : NX == 96 ? 416
                           : NX == 64 ? 288 : 128;
   static constexpr int TW = NX + NX + NY;                 // twx, twxT, twy
   // Phase-4 task order.  Tasks (p, k1) of one half-warp read and write 64-bit words at

@@ -19,7 +19,12 @@ struct Y2 {
   static constexpr int N1 = split_n1(NY), N2 = NY / N1;
   static constexpr int NT = TY * N2;
   static_assert(N1 <= N2, "step B runs on the first TY * N1 threads");
-  static constexpr size_t SMEM = (size_t)(NY + NY * TY) * 8;
+  // Row r of the step-A buffer starts at r TY + (r / N2) PAD.  With TY = 8, a step-B
+  // half-warp reads two blocks of N2 rows; PAD = 8 puts them on opposite bank halves
+  // when N2 TY = 0 (mod 16).
+  static constexpr int PAD = (TY < 16 && (N2 * TY) % 16 == 0) ? 8 : 0;
+  __host__ __device__ static constexpr int row(int r) { return r * TY + (r / N2) * PAD; }
+  static constexpr size_t SMEM = (size_t)(NY + NY * TY + N1 * PAD) * 8;
   // two CTAs per SM where the register budget allows it without spilling the step-B lines
   static constexpr int MINB = N2 <= 24 && NY > 256 ? 2 : 1;
 };
@@ -78,13 +83,13 @@ __global__ void __launch_bounds__(Y2<NY, TY>::NT, Y2<NY, TY>::MINB) k_ypass2(con
       constexpr int k1 = decltype(K1)::value;
       float2 v = a[k1];
       if (k1 > 0) v = INV ? cmulc(v, w[k1]) : cmul(v, w[k1]);
-      b[(j2A + N2 * k1) * TY + mlA] = v;
+      b[C::row(j2A + N2 * k1) + mlA] = v;
     });
     __syncthreads();
     if (N2 <= 16 && s + 1 < NSL) load_a(s + 1);   // in flight during step B (short lines)
     if (hasB) {
       float2 x[N2];
-      sfor<0, N2>([&](auto J2) { x[decltype(J2)::value] = b[(N2 * k1B + decltype(J2)::value) * TY + mlB]; });
+      sfor<0, N2>([&](auto J2) { x[decltype(J2)::value] = b[C::row(N2 * k1B + decltype(J2)::value) + mlB]; });
       RDft<N2, INV>::run(x);
       if (kxB < HX) {
         float2* dst = dst_of(s) + zoff;
@@ -104,10 +109,22 @@ struct X2 {
   static constexpr int NXc = NX, NPCc = NPC;
   static constexpr int HX = NX / 2 + 1;
   static constexpr int AX1 = split_n1(NX), AX2 = NX / AX1;
-  static constexpr int PA = AX2 + 1, PB = AX1 + 1;
-  static constexpr int PST = cmax3(2 * HX, AX1 * PA, AX2 * PB) | 1;
+  // Padded row lengths of the step-A outputs (PA: x-inverse, PB: x-forward) and the pair
+  // stride, per size for the fewest shared-memory wavefronts over all phases (a bank
+  // model of every access).  PST = 2 (mod 16) makes the x-inverse reads and writes
+  // conflict-free: a half-warp there holds eight pairs at two adjacent columns, and the
+  // pair offsets 2p, p < 8, plus 0 or 1 cover the 16 banks once.
+  static constexpr bool T243 = NX == 243 && NPC == 21;
+  static constexpr int PA = T243 ? 33 : AX2 + 1;
+  static constexpr int PB = T243 ? 11 : AX1 + 1;
+  static constexpr int PST_MIN = cmax3(2 * HX, AX1 * PA, AX2 * PB);
+  static constexpr int PST = NX == 480 && NPC == 8 ? 514 : NX == 256 && NPC == 8 ? 274 : T243 ? 297 : (PST_MIN | 1);
+  static_assert(PST >= PST_MIN, "pair regions must not overlap");
   static constexpr int T3 = NPC * AX2, T4 = NPC * AX1, TU = NPC * HX;
-  static constexpr int NT = ((T3 > T4 ? T3 : T4) + 31) / 32 * 32;
+  // one round of the update phase (T4 tasks: step B, field update, forward step A); the
+  // lighter x-inverse step A (T3 tasks) takes one round too unless that would leave more
+  // than half the threads idle in the update
+  static constexpr int NT = ((T3 <= 2 * T4 ? (T3 > T4 ? T3 : T4) : T4) + 31) / 32 * 32;
   static constexpr int TWP = (2 * NX + 1) & ~1;
   static constexpr size_t SMEM = (size_t)(TWP + 2 * NPC * PST) * 8;
   // the shared update functions read old values from global rows here (no staging)

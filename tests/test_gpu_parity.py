@@ -225,7 +225,8 @@ def test_two_step_plane_kernels_gradient_parity(shape, pairing):
     assert oc.rel(g.cpu().numpy().reshape(wl.shape), g_ref) < TOL_GRAD
 
 
-@pytest.mark.parametrize("shape,pairing", [((243, 243, 8), "literal"), ((256, 256, 6), "exact")])
+@pytest.mark.parametrize("shape,pairing", [((243, 243, 8), "literal"), ((256, 256, 6), "exact"),
+                                            ((480, 480, 6), "exact")])
 def test_two_step_split_plane_gradient_parity(shape, pairing):
     """The two-step split-plane kernels (column passes and row-pair passes through global
     memory, schedule specialized = 2 with split planes) against the oracle gradient."""
