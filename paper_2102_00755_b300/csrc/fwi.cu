@@ -466,7 +466,9 @@ fwi_status cuda_fail(cudaError_t e, const char* what) {
   }
 // split planes: y-pass columns per CTA (8 where the 27-point step B needs the register
 // file of a smaller CTA) and x-pass row pairs per CTA
-__host__ __device__ constexpr int ty2_for(int n) { return n / split_n1(n) > 16 ? 8 : 16; }
+// kx columns per CTA of the split y passes: 16 unless the step-B lines are long (8);
+// 243 takes three step-A tasks per thread and 16 columns (see Y2::RA)
+__host__ __device__ constexpr int ty2_for(int n) { return n == 243 || n / split_n1(n) <= 16 ? 16 : 8; }
 // row pairs per CTA of the split x passes: 243 = 9 x 27 gives 9 update tasks per pair,
 // so 21 pairs (6 CTAs for the 122 pairs of a plane) keep the update phase's threads busy
 constexpr int npc2_for(int n) { return n == 243 ? 21 : 8; }

@@ -17,7 +17,12 @@ namespace fwi {
 template <int NY, int TY>
 struct Y2 {
   static constexpr int N1 = split_n1(NY), N2 = NY / N1;
-  static constexpr int NT = TY * N2;
+  // Step A has TY N2 tasks (DFT_N1), step B TY N1 (DFT_N2, the heavy ones).  When N2 is
+  // a multiple N2 = RA N1 with RA > 1 (243 = 9 x 27: RA = 3), a thread takes RA step-A
+  // tasks of its column so that step B fills all TY N1 threads; otherwise one step-A
+  // task per thread and step B on the first TY N1.
+  static constexpr int RA = (N2 % N1 == 0 && N2 / N1 > 1 && N2 > 24) ? N2 / N1 : 1;
+  static constexpr int NT = TY * N2 / RA;
   static_assert(N1 <= N2, "step B runs on the first TY * N1 threads");
   // Row r of the step-A buffer starts at r TY + (r / N2) PAD.  With TY = 8, a step-B
   // half-warp reads two blocks of N2 rows; PAD = 8 puts them on opposite bank halves
@@ -26,7 +31,7 @@ struct Y2 {
   __host__ __device__ static constexpr int row(int r) { return r * TY + (r / N2) * PAD; }
   static constexpr size_t SMEM = (size_t)(NY + NY * TY + N1 * PAD) * 8;
   // two CTAs per SM where the register budget allows it without spilling the step-B lines
-  static constexpr int MINB = N2 <= 24 && NY > 256 ? 2 : 1;
+  static constexpr int MINB = (N2 <= 24 && NY > 256) || RA > 1 ? 2 : 1;
 };
 
 template <int KIND, int NY, int TY>
@@ -55,6 +60,54 @@ __global__ void __launch_bounds__(Y2<NY, TY>::NT, Y2<NY, TY>::MINB) k_ypass2(con
   };
   // the y factor multiplies slot 1 of the inverse passes (a+_y: momentum, a-_y: mass)
   const float2* fac = KIND == Y_INV_MOM ? P.ap[1] : P.am[1];
+  if constexpr (C::RA > 1) {
+    // RA step-A tasks per thread (column mlA, j2 = j2A + r N2 / RA), all loads first
+    constexpr int RA = C::RA;
+    const int ml = threadIdx.x % TY, j2a = threadIdx.x / TY;
+    const int kx = k0 + ml;
+#pragma unroll 1
+    for (int s = 0; s < NSL; ++s) {
+      const float2* src = src_of(s) + zoff;
+      float2 a[RA][N1];
+      sfor<0, RA>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        sfor<0, N1>([&](auto J1) {
+          constexpr int j1 = decltype(J1)::value;
+          const int ky = j2a + (N2 / RA) * r + N2 * j1;
+          float2 v = kx < HX ? src[(size_t)ky * HX + kx] : make_float2(0.f, 0.f);
+          if (INV && s == 1) v = cmul(v, __ldg(&fac[ky]));
+          a[r][j1] = v;
+        });
+      });
+      __syncthreads();   // twiddles staged; the previous slot's buffer consumed
+      sfor<0, RA>([&](auto R) {
+        constexpr int r = decltype(R)::value;
+        const int j2 = j2a + (N2 / RA) * r;
+        RDft<N1, INV>::run(a[r]);
+        float2 w[N1];
+        tw_row<N1>(tw, j2, w);
+        sfor<0, N1>([&](auto K1) {
+          constexpr int k1 = decltype(K1)::value;
+          float2 v = a[r][k1];
+          if (k1 > 0) v = INV ? cmulc(v, w[k1]) : cmul(v, w[k1]);
+          b[C::row(j2 + N2 * k1) + ml] = v;
+        });
+      });
+      __syncthreads();
+      const int k1B = threadIdx.x / TY;
+      float2 x[N2];
+      sfor<0, N2>([&](auto J2) { x[decltype(J2)::value] = b[C::row(N2 * k1B + decltype(J2)::value) + ml]; });
+      RDft<N2, INV>::run(x);
+      if (kx < HX) {
+        float2* dst = dst_of(s) + zoff;
+        sfor<0, N2>([&](auto K2) {
+          constexpr int k2 = decltype(K2)::value;
+          dst[(size_t)(k1B + N1 * k2) * HX + kx] = x[k2];
+        });
+      }
+    }
+    return;
+  }
   const int mlA = threadIdx.x % TY, j2A = threadIdx.x / TY;
   const int kxA = k0 + mlA;
   float2 a[N1];
