@@ -179,12 +179,27 @@ struct X2 {
   // than half the threads idle in the update
   static constexpr int NT = ((T3 <= 2 * T4 ? (T3 > T4 ? T3 : T4) : T4) + 31) / 32 * 32;
   static constexpr int TWP = (2 * NX + 1) & ~1;
-  static constexpr size_t SMEM = (size_t)(TWP + 2 * NPC * PST) * 8;
-  // the shared update functions read old values from global rows here (no staging)
+  // Old field values of the update: staged rows of the pass's 2 NPC rows in shared memory
+  // (STG, where two CTAs per SM still fit), else read from global memory.  Staged rows
+  // are RS floats apart with 2 RS = 20 (mod 32): a warp's update tasks (20 columns per
+  // row pair) then read 32 distinct banks.
+  static constexpr bool STG = NX == 480 && NPC == 8;
+  static constexpr int RS = STG ? 490 : NX;
+  static constexpr size_t SMEM = (size_t)(TWP + 2 * NPC * PST) * 8 + (STG ? (size_t)2 * NPC * RS * 4 : 0);
   static constexpr bool REMAP = false;
-  static constexpr int RS = NX;
-  __host__ __device__ static constexpr int row_off(int y) { return y * NX; }
+  __host__ __device__ static constexpr int row_off(int y) { return y * RS; }
 };
+
+// rows 0 .. nyl-1 of a field (row length NX, this pass's first row at src) -> staged rows
+template <class G>
+__device__ __forceinline__ void x2_stage_old(float* R, const float* __restrict__ src, int nyl) {
+  constexpr int H = G::NXc / 2;   // 8-byte pieces per row (odd staged rows start 8-byte aligned)
+  for (int i = threadIdx.x; i < 2 * G::NPCc * H; i += G::NT) {
+    const int y = i / H, c = i - y * H;
+    if (y < nyl) cp_async8(R + G::row_off(y) + 2 * c, src + y * G::NXc + 2 * c);
+  }
+  cp_async_commit();
+}
 
 template <class G>
 __device__ __forceinline__ void x2_stage_twiddles(float2* tw, const StepParams& P) {
@@ -270,6 +285,7 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mom(const __grid_
   const float2* twxT = xs2 + NX;
   float2* S = xs2 + G::TWP;
   float2* X = S + NPC * G::PST;
+  float* R = reinterpret_cast<float*>(X + NPC * G::PST);   // staged old rows (G::STG)
   const int z = blockIdx.y;
   const SimPtrs& Q = P.sims[blockIdx.z];
   const int ny = P.ny, p0 = blockIdx.x * NPC;
@@ -283,13 +299,15 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mom(const __grid_
   for (int cc = 0; cc < 3; ++cc) {
     const int comp = cc == 0 ? 2 : cc - 1;
     float2* buf = buf_of(comp);
+    float* v = Q.v[comp] + voff;
     cp_async_wait_all();
     __syncthreads();
+    if constexpr (G::STG) x2_stage_old<G>(R, v, nyl);
     x2_xinv_a<G>(X, S, twx, comp == 0 ? P.ap[0] : nullptr, nyl);
+    if constexpr (G::STG) cp_async_wait_all();
     __syncthreads();
-    float* v = Q.v[comp] + voff;
-    p2_mom_update<G, true>(S, X, twxT, v, v, comp == 1 ? P.lams[1] + 2 * p0 : P.lams[comp], comp, lz,
-                     P.dt_over_rho0, nyl);
+    p2_mom_update<G, !G::STG>(S, X, twxT, v, G::STG ? R : v, comp == 1 ? P.lams[1] + 2 * p0 : P.lams[comp], comp,
+                              lz, P.dt_over_rho0, nyl);
     __syncthreads();
     p2_xfwd_b<G>(X, S);
     __syncthreads();
@@ -310,6 +328,7 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mass(const __grid
   const float2* twxT = xs2 + NX;
   float2* S = xs2 + G::TWP;
   float2* X = S + NPC * G::PST;
+  float* R = reinterpret_cast<float*>(X + NPC * G::PST);   // staged old rows (G::STG)
   const int z = blockIdx.y;
   const SimPtrs& Q = P.sims[blockIdx.z];
   const int role = Q.role, shot = Q.shot, tix = P.tidx[blockIdx.z];
@@ -323,19 +342,22 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mass(const __grid
 #pragma unroll 1
   for (int cc = 0; cc < 3; ++cc) {
     const int comp = cc == 0 ? 0 : (cc == 1 ? 2 : 1);
+    float* rg = Q.rho[comp] + voff;
     cp_async_wait_all();
     __syncthreads();
+    if constexpr (G::STG) x2_stage_old<G>(R, rg, nyl);
     x2_xinv_a<G>(X, S, twx, comp == 0 ? P.am[0] : nullptr, nyl);
+    if constexpr (G::STG) cp_async_wait_all();
     __syncthreads();
-    float* rg = Q.rho[comp] + voff;
     const float* lam = comp == 1 ? P.lam[1] + 2 * p0 : P.lam[comp];
+    const float* rin = G::STG ? R : rg;
     if (cc < 2) {
       x2_load_rows<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff, p0, ny);   // overlaps the update
-      p2_mass_update<G, false, true>(S, nullptr, rg, rg, lam, comp, lz, P.dt_rho0, nullptr, nullptr, nullptr,
-                                     nyl);
+      p2_mass_update<G, false, !G::STG>(S, nullptr, rg, rin, lam, comp, lz, P.dt_rho0, nullptr, nullptr, nullptr,
+                                        nyl);
     } else {
-      p2_mass_update<G, true, true>(S, X, rg, rg, lam, comp, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
-                                    P.c2 + voff, nyl);
+      p2_mass_update<G, true, !G::STG>(S, X, rg, rin, lam, comp, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
+                                       P.c2 + voff, nyl);
     }
   }
   __syncthreads();
