@@ -29,7 +29,11 @@ struct Y2 {
   // when N2 TY = 0 (mod 16).
   static constexpr int PAD = (TY < 16 && (N2 * TY) % 16 == 0) ? 8 : 0;
   __host__ __device__ static constexpr int row(int r) { return r * TY + (r / N2) * PAD; }
-  static constexpr size_t SMEM = (size_t)(NY + NY * TY + N1 * PAD) * 8;
+  // Long step-B lines (N2 > 16) leave no registers to prefetch the next slot's step-A
+  // inputs: GST stages them in shared memory with cp.async during the current step B.
+  static constexpr bool GST = RA == 1 && N2 > 16;
+  static constexpr int BSZ = NY * TY + N1 * PAD;          // step-A output buffer
+  static constexpr size_t SMEM = (size_t)(NY + BSZ + (GST ? NY * TY : 0)) * 8;
   // two CTAs per SM where the register budget allows it without spilling the step-B lines
   static constexpr int MINB = (N2 <= 24 && NY > 256) || RA > 1 ? 2 : 1;
 };
@@ -110,25 +114,40 @@ __global__ void __launch_bounds__(Y2<NY, TY>::NT, Y2<NY, TY>::MINB) k_ypass2(con
   }
   const int mlA = threadIdx.x % TY, j2A = threadIdx.x / TY;
   const int kxA = k0 + mlA;
+  float2* g = b + C::BSZ;   // staged inputs [ky][TY] (C::GST)
+  auto stage = [&](int s) {
+    const float2* src = src_of(s) + zoff;
+    for (int i = threadIdx.x; i < NY * TY; i += C::NT) {
+      const int ky = i / TY, ml = i - ky * TY;
+      if (k0 + ml < HX) cp_async8(&g[i], &src[(size_t)ky * HX + k0 + ml]);
+      else g[i] = make_float2(0.f, 0.f);
+    }
+    cp_async_commit();
+  };
   float2 a[N1];
   auto load_a = [&](int s) {
     const float2* src = src_of(s) + zoff;
     sfor<0, N1>([&](auto J1) {
       constexpr int j1 = decltype(J1)::value;
       const int ky = j2A + N2 * j1;
-      float2 v = kxA < HX ? src[(size_t)ky * HX + kxA] : make_float2(0.f, 0.f);
+      float2 v;
+      if constexpr (C::GST) v = g[ky * TY + mlA];
+      else v = kxA < HX ? src[(size_t)ky * HX + kxA] : make_float2(0.f, 0.f);
       if (INV && s == 1) v = cmul(v, __ldg(&fac[ky]));
       a[j1] = v;
     });
   };
-  load_a(0);
+  if constexpr (C::GST) stage(0);
+  else load_a(0);
   const bool hasB = threadIdx.x < TY * N1;
   const int mlB = threadIdx.x % TY, k1B = threadIdx.x / TY;
   const int kxB = k0 + mlB;
 #pragma unroll 1
   for (int s = 0; s < NSL; ++s) {
+    if constexpr (C::GST) cp_async_wait_all();
     __syncthreads();   // twiddles staged; the previous slot's buffer consumed
-    if (N2 > 16 && s > 0) load_a(s);
+    if (C::GST) load_a(s);                          // from the staged inputs
+    else if (N2 > 16 && s > 0) load_a(s);
     RDft<N1, INV>::run(a);
     float2 w[N1];
     tw_row<N1>(tw, j2A, w);
@@ -139,7 +158,11 @@ __global__ void __launch_bounds__(Y2<NY, TY>::NT, Y2<NY, TY>::MINB) k_ypass2(con
       b[C::row(j2A + N2 * k1) + mlA] = v;
     });
     __syncthreads();
-    if (N2 <= 16 && s + 1 < NSL) load_a(s + 1);   // in flight during step B (short lines)
+    if constexpr (C::GST) {
+      if (s + 1 < NSL) stage(s + 1);              // in flight during step B
+    } else if (N2 <= 16 && s + 1 < NSL) {
+      load_a(s + 1);                              // in flight during step B (short lines)
+    }
     if (hasB) {
       float2 x[N2];
       sfor<0, N2>([&](auto J2) { x[decltype(J2)::value] = b[C::row(N2 * k1B + decltype(J2)::value) + mlB]; });
