@@ -40,6 +40,30 @@ def alg_bytes_per_voxel(kernel, nx):
             "plane_mass": 4 * hf + 28.0}[kernel]  # 3 spectra read, P_xy written; rho r/w; c0^2
 
 
+# DRAM bytes per simulation in one launch, read + write, from ncu on the 128x128x64 gradient
+# (launches of one simulation in the forward phase, four stream groups, schedule
+# specialized 2 / z_tile 32 / split_plane 0; ncu replays each launch serialised from a cold
+# L2, and the writes, which stay in the 126 MB L2 until the next kernel, count as ~0).
+# The command and the per-kernel table are in profiles/step_kernels_128x128x64_gradient.md.
+# Valid only for these kernels at this size and schedule; anything else reports null.
+# Each kernel's launches depend only on the knobs listed for it (the plane kernels do not
+# see z_tile, the z passes do not see split_plane).
+TRAFFIC_PER_SIM = {"grid": (128, 128, 64),
+                   "knobs": {"zpass_momentum": {"specialized": 2, "z_tile": 32},
+                             "zpass_mass": {"specialized": 2, "z_tile": 32},
+                             "plane_momentum": {"specialized": 2, "split_plane": 0},
+                             "plane_mass": {"specialized": 2, "split_plane": 0}},
+                   "bytes": {"zpass_momentum": 4.30e6, "plane_momentum": 21.15e6,
+                             "zpass_mass": 12.82e6, "plane_mass": 29.65e6}}
+
+
+def traffic_per_launch(kernel, grid, schedule, sims_per_launch):
+    t = TRAFFIC_PER_SIM
+    if tuple(grid) != t["grid"] or any(schedule.get(k) != v for k, v in t["knobs"][kernel].items()):
+        return None
+    return t["bytes"][kernel] * sims_per_launch
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -453,7 +477,13 @@ def main():
                "sims_per_launch": i_sims / max(i_launches, 1), "stream_groups": 1}
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm,
                 "peak_kind": kind, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
-                "traffic": None, "alg_bytes_per_voxel": bpv,
+                "traffic": traffic_per_launch(dominant, (wl.nx, wl.ny, wl.nz), schedule,
+                                              kern_sims / max(kern_launches, 1)),
+                "traffic_note": ("ncu DRAM read + write bytes per simulation of this kernel, times the "
+                                 "simulations per timed launch; null unless the kernels, grid and schedule "
+                                 "are those of the capture"),
+                "alg_bytes_per_launch": bpv * wl.n_vox * kern_sims / max(kern_launches, 1),
+                "alg_bytes_per_voxel": bpv,
                 "step": {"alg_bytes_per_voxel_step": step_bpv, "achieved": step_gbs, "frac": step_gbs / hbm},
                 "isolated": iso,
                 "note": ("achieved/frac: the kernel's CUDA-event time over the timed region, where its "

@@ -469,9 +469,13 @@ fwi_status cuda_fail(cudaError_t e, const char* what) {
 // kx columns per CTA of the split y passes: 16 unless the step-B lines are long (8);
 // 243 takes three step-A tasks per thread and 16 columns (see Y2::RA)
 __host__ __device__ constexpr int ty2_for(int n) { return n == 243 || n / split_n1(n) <= 16 ? 16 : 8; }
+#ifndef P2_NPC243
+#define P2_NPC243 14
+#endif
 // row pairs per CTA of the split x passes: 243 = 9 x 27 gives 9 update tasks per pair,
-// so 21 pairs (6 CTAs for the 122 pairs of a plane) keep the update phase's threads busy
-constexpr int npc2_for(int n) { return n == 243 ? 21 : 8; }
+// so 14 pairs (126 tasks on 128 threads) keep the update phase's threads busy and leave
+// shared memory for the staged old rows (21 pairs without staging: 20 % slower)
+constexpr int npc2_for(int n) { return n == 243 ? P2_NPC243 : 8; }
 #define S2_DISPATCH(p, CALL)                                            \
   switch ((p)->s2) {                                                    \
     case 243: { constexpr int N = 243; CALL; } break;                   \

@@ -190,7 +190,7 @@ struct X2 {
   // model of every access).  PST = 2 (mod 16) makes the x-inverse reads and writes
   // conflict-free: a half-warp there holds eight pairs at two adjacent columns, and the
   // pair offsets 2p, p < 8, plus 0 or 1 cover the 16 banks once.
-  static constexpr bool T243 = NX == 243 && NPC == 21;
+  static constexpr bool T243 = NX == 243 && (NPC == 21 || NPC == 14);
   static constexpr int PA = T243 ? 33 : AX2 + 1;
   static constexpr int PB = T243 ? 11 : AX1 + 1;
   static constexpr int PST_MIN = cmax3(2 * HX, AX1 * PA, AX2 * PB);
@@ -206,8 +206,8 @@ struct X2 {
   // (STG, where two CTAs per SM still fit), else read from global memory.  Staged rows
   // are RS floats apart with 2 RS = 20 (mod 32): a warp's update tasks (20 columns per
   // row pair) then read 32 distinct banks.
-  static constexpr bool STG = NX == 480 && NPC == 8;
-  static constexpr int RS = STG ? 490 : NX;
+  static constexpr bool STG = (NX == 480 && NPC == 8) || (NX == 243 && NPC == 14);
+  static constexpr int RS = NX == 480 && STG ? 490 : NX == 243 && STG ? 244 : NX;
   static constexpr size_t SMEM = (size_t)(TWP + 2 * NPC * PST) * 8 + (STG ? (size_t)2 * NPC * RS * 4 : 0);
   static constexpr bool REMAP = false;
   __host__ __device__ static constexpr int row_off(int y) { return y * RS; }
@@ -216,10 +216,15 @@ struct X2 {
 // rows 0 .. nyl-1 of a field (row length NX, this pass's first row at src) -> staged rows
 template <class G>
 __device__ __forceinline__ void x2_stage_old(float* R, const float* __restrict__ src, int nyl) {
-  constexpr int H = G::NXc / 2;   // 8-byte pieces per row (odd staged rows start 8-byte aligned)
+  // 8-byte pieces where every row starts 8-byte aligned (even NX and RS), else 4-byte ones
+  constexpr int W = (G::NXc % 2 == 0 && G::RS % 2 == 0) ? 2 : 1;
+  constexpr int H = G::NXc / W;
   for (int i = threadIdx.x; i < 2 * G::NPCc * H; i += G::NT) {
     const int y = i / H, c = i - y * H;
-    if (y < nyl) cp_async8(R + G::row_off(y) + 2 * c, src + y * G::NXc + 2 * c);
+    if (y < nyl) {
+      if constexpr (W == 2) cp_async8(R + G::row_off(y) + 2 * c, src + y * G::NXc + 2 * c);
+      else cp_async4(R + G::row_off(y) + c, src + y * G::NXc + c);
+    }
   }
   cp_async_commit();
 }
