@@ -9,7 +9,7 @@ simulation steps of 2^20 voxels.  Prints one JSON line (rank 0).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle on bounded samples of the same
-workload (the reference arm of this build; the paper ships no code).
+workload (the reference arm: the paper ships no code).
 """
 import argparse
 import json

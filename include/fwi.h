@@ -46,7 +46,7 @@ typedef enum fwi_status {
   FWI_ETIMEOUT = 4,     /* a bounded device wait gave up                           */
   FWI_ECUDA = 5,        /* a CUDA runtime call failed                              */
   FWI_ECANCELLED = 6,   /* work was cancelled before it ran                        */
-  FWI_ENOTSUP = 7       /* grid shape not supported by this build                  */
+  FWI_ENOTSUP = 7       /* grid shape not supported by the library                 */
 } fwi_status;
 
 typedef enum fwi_pairing {
@@ -246,9 +246,9 @@ int64_t fwi_plan_launches(const fwi_plan *plan, int32_t K, int32_t gradient);
 
 /*
  * FFT schedule of a plan (what the autotuner searches).
- *   specialized: 1 = compile-time transforms where this build has them (square planes
+ *   specialized: 1 = compile-time transforms where the library has them (square planes
  *                of 32, 64, 96, 128, 160; z lengths 32..128), 0 = runtime schedules,
- *                2 = two-step register-transform kernels where this build has them:
+ *                2 = two-step register-transform kernels where the library has them:
  *                whole square planes of 32, 64, 96, 128, 135, 160; split square planes of
  *                243, 256, 480; z lengths 32, 48, 64, 80, 96, 128, 135, 256 (the other
  *                passes as for 1; FWI_ENOTSUP when none applies)
