@@ -64,6 +64,35 @@ def traffic_per_launch(kernel, grid, schedule, sims_per_launch):
     return t["bytes"][kernel] * sims_per_launch
 
 
+# Multi-GPU use is replicas only: each rank computes its own encoded gradient estimate
+# (Sec. 4.5) with no data-path collective; the job is timed as the slowest rank.
+def replica_weights(weights, rank):
+    """Encoding weights [K][n_src] of one replica: rank 0 keeps the workload's own, every other
+    rank draws its own Rademacher super-shots (an independent gradient estimate)."""
+    if rank == 0:
+        return weights
+    from paper_2102_00755_b300 import synth
+    rng = np.random.default_rng(1000 + rank)
+    return np.stack([synth.rademacher(weights.shape[1], rng) for _ in range(weights.shape[0])])
+
+
+def job_time_ms(local_ms, world, device=None):
+    """Max over ranks of one rank's timed region (ms); needs an initialised process group
+    when world > 1."""
+    if world == 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, world, steps, job_ms):
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return units_per_rank_step * world * steps / (job_ms / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -380,9 +409,7 @@ def main():
         f"serving level {args.level}: one TR gradient (one super-shot of 8 emitters, 1024 receivers) "
         f"on the {wl.nx}x{wl.ny}x{wl.nz} grid, {wl.nt} steps")
     K = wl.weights.shape[0]
-    if rank > 0:   # independent estimates per GPU (Sec. 4.5): other encoding weights
-        rng = np.random.default_rng(1000 + rank)
-        wl.weights = np.stack([synth.rademacher(len(wl.src_idx), rng) for _ in range(K)])
+    wl.weights = replica_weights(wl.weights, rank)   # independent estimates per GPU (Sec. 4.5)
     from paper_2102_00755_b300 import autotune
     if args.schedule:
         schedule = dict(zip(autotune.KNOBS, (int(v) for v in args.schedule.split(","))))
@@ -441,13 +468,9 @@ def main():
     plan.profile(dominant, enable=False)
     kern_ms, kern_launches, kern_sims = plan.profile_read()[dominant]
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = vsteps * world * args.steps / (tot_ms / 1e3) / 1e9
-    grads_per_h = 3600.0 * world * args.steps / (tot_ms / 1e3)
+    tot_ms = job_time_ms(sum(step_ms), world, dev)
+    value = whole_job_rate(vsteps, world, args.steps, tot_ms) / 1e9
+    grads_per_h = 3600.0 * whole_job_rate(1, world, args.steps, tot_ms)
     clocks = clk.summary()
     assert plan.status() == fwi.FWI_OK
 
@@ -539,15 +562,11 @@ def main():
             if i > 0:
                 et.append(a.elapsed_time(b))
             flush.zero_()
-        ems = sum(et) / len(et)
-        if world > 1:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = job_time_ms(sum(et) / len(et), world, dev)
         h2d = hc.numel() * 4 + hw.numel() * 4 + ho.numel() * 4
-        e2e = {"value": vsteps * world / (ems / 1e3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": whole_job_rate(vsteps, world, 1, ems) / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": hm.numel() * 8 + hg.numel() * 8, "ms_per_step": ems,
-               "gradients_per_h": 3600.0 * world / (ems / 1e3)}
+               "gradients_per_h": 3600.0 * whole_job_rate(1, world, 1, ems)}
 
     if rank != 0:
         if world > 1:
