@@ -116,8 +116,11 @@ class Server:
         self.levels = {lv.name: lv for lv in levels}
         self.device = torch.device(device)
         self.max_inflight = max_inflight
-        free, _ = torch.cuda.mem_get_info(self.device)
-        self.mem_budget = int(0.9 * free) if mem_budget is None else int(mem_budget)
+        if mem_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            self.mem_budget = int(0.9 * free)
+        else:
+            self.mem_budget = int(mem_budget)
         self.pairing = pairing
         self.use_graphs = use_graphs
         self.pool: Dict[str, List[_Slot]] = {name: [] for name in self.levels}
