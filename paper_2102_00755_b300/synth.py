@@ -323,7 +323,9 @@ def serving_level(level: int, n_src: int, seed: int, n_rec: int = 1024, pz: int 
     rng = np.random.default_rng(seed)
     # breast in the physical region, bowl radius 0.473 of the physical width
     z_e = P[2] + pz - 2
-    R = min(0.473 * px, z_e - 1.0)       # the bowl must fit the grid when z is overridden
+    # the bowl must stay in the physical region when z is overridden (its lowest point on
+    # the first physical plane); for the levels' own extents 0.473 px is the smaller
+    R = min(0.473 * px, float(z_e - P[2]))
     centre = (nx / 2.0, ny / 2.0, float(z_e))
     semi = (0.7 * 0.7 * R, 0.7 * 0.7 * R, 0.8 * 0.7 * R)
     gamma = half_ellipsoid_mask(shp, centre, semi)
