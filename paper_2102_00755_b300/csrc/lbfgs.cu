@@ -62,7 +62,8 @@ __global__ void k_loop2(int64_t n, const double* __restrict__ part, int np, doub
     r[i] += c * (double)s[i];
 }
 
-__global__ void k_scale_copy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ out) {
+// out = a x; also called in place (x == out): no __restrict__ on either pointer
+__global__ void k_scale_copy(int64_t n, double a, const double* x, double* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = a * x[i];
 }
