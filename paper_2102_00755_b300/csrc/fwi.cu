@@ -14,6 +14,7 @@
 
 #include "../../include/fwi.h"
 #include "kernels.cuh"
+#include "launch.cuh"
 #include "plane2.cuh"
 #include "split2.cuh"
 
@@ -464,18 +465,6 @@ fwi_status cuda_fail(cudaError_t e, const char* what) {
     case 256: { constexpr int NZ = 256; CALL; } break;                  \
     default: break;                                                     \
   }
-// split planes: y-pass columns per CTA (8 where the 27-point step B needs the register
-// file of a smaller CTA) and x-pass row pairs per CTA
-// kx columns per CTA of the split y passes: 16 unless the step-B lines are long (8);
-// 243 takes three step-A tasks per thread and 16 columns (see Y2::RA)
-__host__ __device__ constexpr int ty2_for(int n) { return n == 243 || n / split_n1(n) <= 16 ? 16 : 8; }
-#ifndef P2_NPC243
-#define P2_NPC243 14
-#endif
-// row pairs per CTA of the split x passes: 243 = 9 x 27 gives 9 update tasks per pair,
-// so 14 pairs (126 tasks on 128 threads) keep the update phase's threads busy and leave
-// shared memory for the staged old rows (21 pairs without staging: 20 % slower)
-constexpr int npc2_for(int n) { return n == 243 ? P2_NPC243 : 8; }
 #define S2_DISPATCH(p, CALL)                                            \
   switch ((p)->s2) {                                                    \
     case 243: { constexpr int N = 243; CALL; } break;                   \
@@ -513,56 +502,15 @@ int smem_optin_max() {
   return v > 0 ? v : 48 * 1024;
 }
 
-template <int E, int F>
-void set_attrs_plane(int cap) {
-  cudaFuncSetAttribute(k_plane_mom<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_plane_mass<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_tr_init<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-}
-template <int N>
-void set_attrs_p2(int cap) {
-  cudaFuncSetAttribute(k_plane2_mom<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_plane2_mass<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-}
-template <int N>
-void set_attrs_s2(int cap) {
-  cudaFuncSetAttribute(k_ypass2<Y_INV_MOM, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass2<Y_INV_MASS, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass2<Y_FWD3, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass2<Y_FWD1, N, ty2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass2_mom<N, npc2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass2_mass<N, npc2_for(N)>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-}
-template <int NZ, int TZ>
-void set_attrs_z2(int cap) {
-  cudaFuncSetAttribute(k_zpass2<0, NZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_zpass2<1, NZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-}
-template <int E, int FZ, int TZ>
-void set_attrs_z(int cap) {
-  cudaFuncSetAttribute(k_zpass<0, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_zpass<1, E, FZ, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-}
-template <int E>
-void set_attrs_split(int cap) {
-  cudaFuncSetAttribute(k_ypass<Y_INV_MOM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass<Y_INV_MASS, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass<Y_FWD3, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass<Y_FWD1, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass_mom<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass_mass<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass_tr_init<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-}
-
 void set_attrs(fwi_plan* p) {
   const int cap = smem_optin_max();
-  if (p->epl == 8) set_attrs_split<8>(cap);
-  else set_attrs_split<16>(cap);
-  PLANE_DISPATCH(p, (set_attrs_plane<E, F>(cap)));
-  P2_DISPATCH(p, (set_attrs_p2<N>(cap)));
-  Z2_DISPATCH(p, (set_attrs_z2<NZ, TZ>(cap)));
-  S2_DISPATCH(p, (set_attrs_s2<N>(cap)));
-  Z_DISPATCH(p, (set_attrs_z<E, FZ, TZ>(cap)));
+  if (p->epl == 8) attrs_split<8>(cap);
+  else attrs_split<16>(cap);
+  PLANE_DISPATCH(p, (attrs_plane<E, F>(cap)));
+  P2_DISPATCH(p, (attrs_plane2<N>(cap)));
+  Z2_DISPATCH_T(p, 0, (attrs_zpass2<NZ>(cap)));
+  S2_DISPATCH(p, (attrs_split2<N>(cap)));
+  Z_DISPATCH_T(p, 0, (attrs_zpass<E, FZ>(cap)));
   // Touch every small kernel too, so that modules are loaded before any stream
   // capture of a call (a first launch inside a capture may not load them).
   cudaFuncAttributes a;
@@ -605,53 +553,53 @@ fwi_status launch_step_split(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   int slot;
   prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
   if (p->z2) {
-    Z2_DISPATCH(p, (k_zpass2<0, NZ, TZ><<<gz, Z2<NZ, TZ>::NT, p->smem_z2[0], st>>>(P)));
+    Z2_DISPATCH(p, (launch_zpass2<NZ>(0, TZ, gz, p->smem_z2[0], st, P)));
     LAUNCHED("k_zpass2<momentum>");
   } else {
-    Z_DISPATCH(p, (k_zpass<0, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+    Z_DISPATCH(p, (launch_zpass<E, FZ>(0, TZ, gz, p->smem_zmom, st, P)));
     LAUNCHED("k_zpass<momentum>");
   }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
   if (p->s2) {
-    S2_DISPATCH(p, (k_ypass2<Y_INV_MOM, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
+    S2_DISPATCH(p, (launch_split2<N>(Y_INV_MOM, gy2, p->smem_y2, st, P)));
     LAUNCHED("k_ypass2<inverse, momentum>");
-    S2_DISPATCH(p, (k_xpass2_mom<N, npc2_for(N)><<<gx2b, X2<N, npc2_for(N)>::NT, p->smem_x2, st>>>(P)));
+    S2_DISPATCH(p, (launch_split2<N>(4, gx2b, p->smem_x2, st, P)));
     LAUNCHED("k_xpass2_mom");
-    S2_DISPATCH(p, (k_ypass2<Y_FWD3, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
+    S2_DISPATCH(p, (launch_split2<N>(Y_FWD3, gy2, p->smem_y2, st, P)));
     LAUNCHED("k_ypass2<forward x3>");
   } else {
-    k_ypass<Y_INV_MOM, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
+    launch_split<EL>(Y_INV_MOM, gy, p->smem_ypass3, st, P);
     LAUNCHED("k_ypass<inverse, momentum>");
-    k_xpass_mom<EL><<<gx1, kTpbPlane, p->smem_xmom, st>>>(P);
+    launch_split<EL>(4, gx1, p->smem_xmom, st, P);
     LAUNCHED("k_xpass_mom");
-    k_ypass<Y_FWD3, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
+    launch_split<EL>(Y_FWD3, gy, p->smem_ypass3, st, P);
     LAUNCHED("k_ypass<forward x3>");
   }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
   if (p->z2) {
-    Z2_DISPATCH(p, (k_zpass2<1, NZ, TZ><<<gz, Z2<NZ, TZ>::NT, p->smem_z2[1], st>>>(P)));
+    Z2_DISPATCH(p, (launch_zpass2<NZ>(1, TZ, gz, p->smem_z2[1], st, P)));
     LAUNCHED("k_zpass2<mass>");
   } else {
-    Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+    Z_DISPATCH(p, (launch_zpass<E, FZ>(1, TZ, gz, p->smem_zmass, st, P)));
     LAUNCHED("k_zpass<mass>");
   }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
   if (p->s2) {
-    S2_DISPATCH(p, (k_ypass2<Y_INV_MASS, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
+    S2_DISPATCH(p, (launch_split2<N>(Y_INV_MASS, gy2, p->smem_y2, st, P)));
     LAUNCHED("k_ypass2<inverse, mass>");
-    S2_DISPATCH(p, (k_xpass2_mass<N, npc2_for(N)><<<gx2b, X2<N, npc2_for(N)>::NT, p->smem_x2, st>>>(P)));
+    S2_DISPATCH(p, (launch_split2<N>(5, gx2b, p->smem_x2, st, P)));
     LAUNCHED("k_xpass2_mass");
-    S2_DISPATCH(p, (k_ypass2<Y_FWD1, N, ty2_for(N)><<<gy2, Y2<N, ty2_for(N)>::NT, p->smem_y2, st>>>(P)));
+    S2_DISPATCH(p, (launch_split2<N>(Y_FWD1, gy2, p->smem_y2, st, P)));
     LAUNCHED("k_ypass2<forward x1>");
   } else {
-    k_ypass<Y_INV_MASS, EL><<<gy, kTpbZ, p->smem_ypass3, st>>>(P);
+    launch_split<EL>(Y_INV_MASS, gy, p->smem_ypass3, st, P);
     LAUNCHED("k_ypass<inverse, mass>");
-    k_xpass_mass<EL><<<gx2, kTpbPlane, p->smem_xmass, st>>>(P);
+    launch_split<EL>(5, gx2, p->smem_xmass, st, P);
     LAUNCHED("k_xpass_mass");
-    k_ypass<Y_FWD1, EL><<<gy, kTpbZ, p->smem_ypass1, st>>>(P);
+    launch_split<EL>(Y_FWD1, gy, p->smem_ypass1, st, P);
     LAUNCHED("k_ypass<forward x1>");
   }
   prof_end(p, st, slot);
@@ -665,37 +613,37 @@ fwi_status launch_step_batch(fwi_plan* p, const StepParams& P, cudaStream_t st) 
   int slot;
   prof_begin(p, FWI_K_ZPASS_MOMENTUM, st, P.nsims, &slot);
   if (p->z2) {
-    Z2_DISPATCH(p, (k_zpass2<0, NZ, TZ><<<gz, Z2<NZ, TZ>::NT, p->smem_z2[0], st>>>(P)));
+    Z2_DISPATCH(p, (launch_zpass2<NZ>(0, TZ, gz, p->smem_z2[0], st, P)));
     LAUNCHED("k_zpass2<momentum>");
   } else {
-    Z_DISPATCH(p, (k_zpass<0, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmom, st>>>(P)));
+    Z_DISPATCH(p, (launch_zpass<E, FZ>(0, TZ, gz, p->smem_zmom, st, P)));
     LAUNCHED("k_zpass<momentum>");
   }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MOMENTUM, st, P.nsims, &slot);
   if (p->p2) {
-    P2_DISPATCH(p, (k_plane2_mom<N, N><<<gp, Plane2<N, N>::NT, p->smem_p2, st>>>(P)));
+    P2_DISPATCH(p, (launch_plane2<N>(0, gp, p->smem_p2, st, P)));
     LAUNCHED("k_plane2_mom");
   } else {
-    PLANE_DISPATCH(p, (k_plane_mom<E, F, F><<<gp, kTpbPlane, p->smem_plane, st>>>(P)));
+    PLANE_DISPATCH(p, (launch_plane<E, F>(0, gp, p->smem_plane, st, P)));
     LAUNCHED("k_plane_mom");
   }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_ZPASS_MASS, st, P.nsims, &slot);
   if (p->z2) {
-    Z2_DISPATCH(p, (k_zpass2<1, NZ, TZ><<<gz, Z2<NZ, TZ>::NT, p->smem_z2[1], st>>>(P)));
+    Z2_DISPATCH(p, (launch_zpass2<NZ>(1, TZ, gz, p->smem_z2[1], st, P)));
     LAUNCHED("k_zpass2<mass>");
   } else {
-    Z_DISPATCH(p, (k_zpass<1, E, FZ, TZ><<<gz, kTpbZ, p->smem_zmass, st>>>(P)));
+    Z_DISPATCH(p, (launch_zpass<E, FZ>(1, TZ, gz, p->smem_zmass, st, P)));
     LAUNCHED("k_zpass<mass>");
   }
   prof_end(p, st, slot);
   prof_begin(p, FWI_K_PLANE_MASS, st, P.nsims, &slot);
   if (p->p2) {
-    P2_DISPATCH(p, (k_plane2_mass<N, N><<<gp, Plane2<N, N>::NT, p->smem_p2, st>>>(P)));
+    P2_DISPATCH(p, (launch_plane2<N>(1, gp, p->smem_p2, st, P)));
     LAUNCHED("k_plane2_mass");
   } else {
-    PLANE_DISPATCH(p, (k_plane_mass<E, F, F><<<gp, kTpbPlane, p->smem_mass, st>>>(P)));
+    PLANE_DISPATCH(p, (launch_plane<E, F>(1, gp, p->smem_mass, st, P)));
     LAUNCHED("k_plane_mass");
   }
   prof_end(p, st, slot);
@@ -1207,18 +1155,18 @@ fwi_status gradient_impl(fwi_plan* p, const float* c, const float* weights, cons
     const dim3 gy((p->hx + kTY - 1) / kTY, q.nz, K);
     if (p->epl == 8) {
       const int g = std::max(1, 16 * 8 / p->hx);
-      k_xpass_tr_init<8><<<dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), kTpbPlane, p->smem_xmom, st>>>(T);
+      launch_split<8>(6, dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), p->smem_xmom, st, T);
       LAUNCHED("k_xpass_tr_init");
-      k_ypass<Y_FWD1, 8><<<gy, kTpbZ, p->smem_ypass1, st>>>(T);
+      launch_split<8>(Y_FWD1, gy, p->smem_ypass1, st, T);
     } else {
       const int g = std::max(1, 16 * 16 / p->hx);
-      k_xpass_tr_init<16><<<dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), kTpbPlane, p->smem_xmom, st>>>(T);
+      launch_split<16>(6, dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), p->smem_xmom, st, T);
       LAUNCHED("k_xpass_tr_init");
-      k_ypass<Y_FWD1, 16><<<gy, kTpbZ, p->smem_ypass1, st>>>(T);
+      launch_split<16>(Y_FWD1, gy, p->smem_ypass1, st, T);
     }
     LAUNCHED("k_ypass<forward x1>");
   } else {
-    PLANE_DISPATCH(p, (k_tr_init<E, F, F><<<dim3(q.nz, K), kTpbPlane, p->smem_plane, st>>>(T)));
+    PLANE_DISPATCH(p, (launch_plane<E, F>(2, dim3(q.nz, K), p->smem_plane, st, T)));
     LAUNCHED("k_tr_init");
   }
   if ((s = launch_step(p, T, st)) != FWI_OK) return s;

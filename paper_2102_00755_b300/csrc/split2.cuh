@@ -14,6 +14,17 @@
 
 namespace fwi {
 
+// kx columns per CTA of the split y passes: 16 unless the step-B lines are long (8);
+// 243 takes three step-A tasks per thread and 16 columns (see Y2::RA)
+__host__ __device__ constexpr int ty2_for(int n) { return n == 243 || n / split_n1(n) <= 16 ? 16 : 8; }
+#ifndef P2_NPC243
+#define P2_NPC243 14
+#endif
+// row pairs per CTA of the split x passes: 243 = 9 x 27 gives 9 update tasks per pair,
+// so 14 pairs (126 tasks on 128 threads) keep the update phase's threads busy and leave
+// shared memory for the staged old rows (21 pairs without staging: 20 % slower)
+constexpr int npc2_for(int n) { return n == 243 ? P2_NPC243 : 8; }
+
 template <int NY, int TY>
 struct Y2 {
   static constexpr int N1 = split_n1(NY), N2 = NY / N1;
