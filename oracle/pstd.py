@@ -33,6 +33,10 @@ Readings where the paper is silent (all listed in the design notes):
   (forward states before step 0 are zero).
 * history=True replaces the TR re-simulation by the stored forward field on
   Gamma (the paper's "full" gradient, Table 2).
+* tr_box restricts the TR re-simulation to a box enclosing Gamma (Sec. 3.1: the TR
+  simulation domain only needs to enclose Gamma).  The box is a grid of its own
+  with the same dx, dt and c_ref, its own PML inside it (same profile rule), and c0
+  cropped from the full model; the boundary layer and Gamma keep their order.
 
 Arrays are shaped (nz, ny, nx), x fastest, linear index i + nx*(j + ny*k).
 Component order xi = (x, y, z) maps to array axes (2, 1, 0).
@@ -235,8 +239,34 @@ def adjoint_source(f, f_obs):
     return D, Q
 
 
+def box_indices(shape, origin, size, idx):
+    """Linear indices idx of a grid of `shape` (nz, ny, nx) -> linear indices of the box of
+    `size` (nx', ny', nz') whose first voxel is `origin` (x0, y0, z0).  Every voxel must lie
+    inside the box.  Cropping keeps the (z, y, x) order, so sorted lists stay sorted."""
+    nz, ny, nx = shape
+    idx = np.asarray(idx, dtype=np.int64)
+    x = idx % nx
+    y = (idx // nx) % ny
+    z = idx // (nx * ny)
+    xb, yb, zb = x - origin[0], y - origin[1], z - origin[2]
+    if np.any((xb < 0) | (xb >= size[0]) | (yb < 0) | (yb >= size[1]) | (zb < 0) | (zb >= size[2])):
+        raise ValueError("a voxel lies outside the TR box")
+    return xb + size[0] * (yb + size[1] * zb)
+
+
+def tr_grid(G: Grid, c: np.ndarray, tr_box, pml_alpha=2.0):
+    """Grid and cropped sound speed of the TR box (origin, size, pml), see `gradient`."""
+    origin, size, pml = tr_box
+    Gb = Grid(size[0], size[1], size[2], G.dx, G.dt, G.c_ref, G.rho0, pml, pml_alpha)
+    x0, y0, z0 = origin
+    cb = c[z0:z0 + size[2], y0:y0 + size[1], x0:x0 + size[0]]
+    if cb.shape != Gb.shape:
+        raise ValueError("the TR box must lie inside the grid")
+    return Gb, np.ascontiguousarray(cb)
+
+
 def gradient(G: Grid, c: np.ndarray, f, f_obs, rec_idx, layer_idx, gamma_idx, g,
-             pairing="literal", history=None, c_rec=None):
+             pairing="literal", history=None, c_rec=None, tr_box=None, pml_alpha=2.0):
     """Misfit and sound-speed gradient of Alg. 1 (second part).
 
     f, f_obs: simulated and observed (encoded) traces [nt, n_rec]; g: boundary
@@ -244,7 +274,9 @@ def gradient(G: Grid, c: np.ndarray, f, f_obs, rec_idx, layer_idx, gamma_idx, g,
     grid's shape and is zero outside Gamma.  With c_rec given the raw Alg. 1
     accumulator is multiplied by dx * c_rec / 2, which makes the exact pairing
     equal dD/dc when every receiver sits in a medium of speed c_rec (without
-    PML); without it the raw accumulator is returned.
+    PML); without it the raw accumulator is returned.  tr_box = (origin (x0, y0, z0),
+    size (nx', ny', nz'), pml (px, py, pz)) runs the TR re-simulation on that box only
+    (its own PML of strength pml_alpha inside it); None runs it on the whole grid.
     """
     nt = f.shape[0]
     Nt = nt - 1
@@ -258,20 +290,27 @@ def gradient(G: Grid, c: np.ndarray, f, f_obs, rec_idx, layer_idx, gamma_idx, g,
     # TR side: P(m) ~ p(t_(Nt-m)) on Gamma for m = 0, 1, 2, ...
     if history is None:
         layer_idx = np.asarray(layer_idx)
-        T = State(G.shape)
-        T.p.reshape(-1)[layer_idx] = g[Nt]                 # initial value on dGamma
         gs = g / (3.0 * cf[layer_idx] ** 2)                # pressure -> split density
+        if tr_box is None:                                 # TR on the whole grid
+            GT, c2T, layT, gamT = G, c2, layer_idx, gamma_idx
+        else:                                              # TR on a box enclosing Gamma
+            GT, cT = tr_grid(G, c, tr_box, pml_alpha)
+            c2T = cT * cT
+            layT = box_indices(G.shape, tr_box[0], tr_box[1], layer_idx)
+            gamT = box_indices(G.shape, tr_box[0], tr_box[1], gamma_idx)
+        T = State(GT.shape)
+        T.p.reshape(-1)[layT] = g[Nt]                      # initial value on dGamma
         m_done = [0]
 
         def tr_next():
             m = m_done[0] + 1
             if m > Nt:
                 return np.zeros(len(gamma_idx))
-            step(G, T, c2, dirichlet=(layer_idx, gs[Nt - m]))
+            step(GT, T, c2T, dirichlet=(layT, gs[Nt - m]))
             m_done[0] = m
-            return T.p.reshape(-1)[gamma_idx].copy()
+            return T.p.reshape(-1)[gamT].copy()
 
-        p_m0 = T.p.reshape(-1)[gamma_idx].copy()
+        p_m0 = T.p.reshape(-1)[gamT].copy()
     else:
         m_done = [0]
 
@@ -308,16 +347,18 @@ def gradient(G: Grid, c: np.ndarray, f, f_obs, rec_idx, layer_idx, gamma_idx, g,
 
 
 def fwi_gradient(G: Grid, c, src_idx, weights, wavelet, rec_idx, layer_idx, gamma_idx, f_obs,
-                 pairing="literal", c_rec=None, full=False, delays=None):
+                 pairing="literal", c_rec=None, full=False, delays=None, tr_box=None, pml_alpha=2.0):
     """Forward + gradient for one encoded super-shot (weights [n_src]; delays [n_src] in
-    time steps for the delayed encoding of Eq. 13, f_obs then encoded with the same delays)."""
+    time steps for the delayed encoding of Eq. 13, f_obs then encoded with the same delays;
+    tr_box: TR re-simulation on a box enclosing Gamma, see `gradient`)."""
     if full:
         f, g, hist = forward(G, c, src_idx, weights, wavelet, rec_idx, layer_idx, gamma_idx=gamma_idx,
                              delays=delays)
         return (f,) + gradient(G, c, f, f_obs, rec_idx, layer_idx, gamma_idx, g, pairing,
                                history=hist, c_rec=c_rec)
     f, g = forward(G, c, src_idx, weights, wavelet, rec_idx, layer_idx, delays=delays)
-    return (f,) + gradient(G, c, f, f_obs, rec_idx, layer_idx, gamma_idx, g, pairing, c_rec=c_rec)
+    return (f,) + gradient(G, c, f, f_obs, rec_idx, layer_idx, gamma_idx, g, pairing, c_rec=c_rec,
+                           tr_box=tr_box, pml_alpha=pml_alpha)
 
 
 def grid_for(wl, pml_on=True):

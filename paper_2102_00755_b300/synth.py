@@ -275,6 +275,39 @@ def config4() -> Workload:
     return phantom_workload("diff-96x96x48", 96, 96, 48, 1000, 32, 128, 1, 100, (101,))
 
 
+def smooth_235(n: int) -> bool:
+    for f in (2, 3, 5):
+        while n % f == 0:
+            n //= f
+    return n == 1
+
+
+def tr_box(wl: "Workload", margin: int, pml: int, sizes=None):
+    """Box for the TR re-simulation restricted to a region enclosing Gamma (Sec. 3.1):
+    Gamma's bounding box grown by `margin` cells and a PML of `pml` cells on every side,
+    each extent rounded up to the first size in `sizes` (default: 2-3-5-smooth sizes),
+    centred on Gamma and kept inside the grid.  Returns (origin, size, pml) as (x, y, z)
+    triples, the argument of Plan(tr_box=...) and of the oracle's tr_box."""
+    gi = np.asarray(wl.gamma_idx, dtype=np.int64)
+    x, y, z = gi % wl.nx, (gi // wl.nx) % wl.ny, gi // (wl.nx * wl.ny)
+    lo = [int(x.min()), int(y.min()), int(z.min())]
+    hi = [int(x.max()), int(y.max()), int(z.max())]
+    n = [wl.nx, wl.ny, wl.nz]
+    origin, size = [], []
+    for a in range(3):
+        need = hi[a] - lo[a] + 1 + 2 * (margin + pml)
+        cand = [s for s in (sizes if sizes is not None else range(need, n[a] + 1)) if s >= need and s <= n[a]]
+        cand = [s for s in cand if smooth_235(s)]
+        m = min(cand) if cand else n[a]
+        o = lo[a] - (m - (hi[a] - lo[a] + 1)) // 2
+        o = min(max(o, 0), n[a] - m)
+        if lo[a] - o < pml or o + m - 1 - hi[a] < pml:
+            raise ValueError("Gamma does not fit inside the TR box's PML-free interior")
+        origin.append(o)
+        size.append(m)
+    return tuple(origin), tuple(size), (pml, pml, pml)
+
+
 def encoding_draws(seed: int, K: int, n_src: int, tau: int = 0):
     """Rademacher weights [K][n_src] and delays [K][n_src] (whole time steps, d ~ U[0, 1]
     times tau, rounded; zero when tau = 0) of the stochastic approximation number `seed`
@@ -310,12 +343,15 @@ SERVING_LEVELS = {
 }
 
 
-def serving_level(level: int, n_src: int, seed: int, n_rec: int = 1024, pz: int = None) -> Workload:
+def serving_level(level: int, n_src: int, seed: int, n_rec: int = 1024, pz: int = None,
+                  nt: int = None) -> Workload:
     """A multigrid level of the serving stream: physical grid padded by the PML
     size rule, Ricker frequency scaled with dx (1 MHz at 0.5 mm).  `pz` replaces the
-    physical z extent (a thinner grid with the same planes, for profiling)."""
-    (px, py, pz0), dx, nt = SERVING_LEVELS[level]
+    physical z extent (a thinner grid with the same planes, for profiling); `nt`
+    replaces the level's number of time steps (a shorter window of the same pulse)."""
+    (px, py, pz0), dx, nt0 = SERVING_LEVELS[level]
     pz = pz0 if pz is None else pz
+    nt = nt0 if nt is None else nt
     P = [optimal_pml(n) for n in (px, py, pz)]
     nx, ny, nz = px + 2 * P[0], py + 2 * P[1], pz + 2 * P[2]
     shp = (nx, ny, nz)

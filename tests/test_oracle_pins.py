@@ -327,6 +327,69 @@ def test_tr_error_decreases_with_layer_thickness():
     assert errs[1] < 0.5 * errs[0], errs
 
 
+# TR re-simulation on a box enclosing Gamma (Sec. 3.1)
+def _tr_box_case():
+    wl = synth.small_workload(36, 36, 30, 90, pml=4, n_src=3, n_rec=30, K=1, layer=3, seed=5, f0=0.4e6,
+                              gamma_frac=0.25)
+    G = pstd.grid_for(wl)
+    w = wl.weights[0]
+    f_obs = pstd.forward(G, wl.c_true, wl.src_idx, w, wl.wavelet, wl.rec_idx)[0]
+    f, g, hist = pstd.forward(G, wl.c_model, wl.src_idx, w, wl.wavelet, wl.rec_idx, wl.layer_idx,
+                              gamma_idx=wl.gamma_idx)
+
+    def grad(**kw):
+        return pstd.gradient(G, wl.c_model, f, f_obs, wl.rec_idx, wl.layer_idx, wl.gamma_idx, g,
+                             c_rec=wl.c_rec, **kw)[1]
+    return wl, grad, hist
+
+
+def test_tr_box_covering_the_grid_is_the_whole_grid_tr():
+    """A box equal to the grid, with the grid's PML, is the whole-grid TR bit for bit
+    (the cropping and index mapping are the identity)."""
+    wl, grad, _ = _tr_box_case()
+    box = ((0, 0, 0), (wl.nx, wl.ny, wl.nz), wl.pml)
+    assert np.array_equal(grad(tr_box=box), grad())
+
+
+def test_tr_box_equals_stored_field_when_layer_covers_gamma():
+    """With the boundary layer covering all of Gamma the TR values on Gamma are the imposed
+    forward values, on any box: the box gradient equals the stored-field gradient.  A wrong
+    mapping of the layer or Gamma into the box breaks this."""
+    wl = synth.small_workload(20, 20, 18, 60, pml=3, layer=6, n_src=2, n_rec=20, K=1, seed=3)
+    assert len(wl.layer_idx) == len(wl.gamma_idx)
+    G = pstd.grid_for(wl)
+    f_obs, _ = pstd.forward(G, wl.c_true, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx)
+    args = (G, wl.c_model, wl.src_idx, wl.weights[0], wl.wavelet, wl.rec_idx, wl.layer_idx,
+            wl.gamma_idx, f_obs)
+    box = synth.tr_box(wl, 1, 2)
+    assert box[1] != (wl.nx, wl.ny, wl.nz) and box[0] != (0, 0, 0)
+    for pairing in ("literal", "exact"):
+        _, D1, g_box = pstd.fwi_gradient(*args, pairing=pairing, tr_box=box)
+        _, D2, g_full = pstd.fwi_gradient(*args, pairing=pairing, full=True)
+        assert D1 == D2
+        assert np.abs(g_box - g_full).max() < 1e-12 * np.abs(g_full).max()
+
+
+def test_tr_box_converges_to_whole_grid_tr_as_margin_grows():
+    """The box only changes what lies outside the boundary layer; the non-local k-space
+    operator feels it across the layer.  Growing the margin between Gamma and the box's PML
+    brings the box gradient monotonically closer to the whole-grid TR gradient, and its
+    error against the stored-field gradient stays that of the whole-grid TR."""
+    wl, grad, hist = _tr_box_case()
+    g_tr = grad()
+    g_full = grad(history=hist)
+    e_tr = np.linalg.norm(g_tr - g_full) / np.linalg.norm(g_full)
+    diffs = []
+    for m in (0, 2, 4, 6):
+        box = synth.tr_box(wl, m, 3)
+        g_box = grad(tr_box=box)
+        diffs.append(np.linalg.norm(g_box - g_tr) / np.linalg.norm(g_tr))
+        e_box = np.linalg.norm(g_box - g_full) / np.linalg.norm(g_full)
+        assert abs(e_box - e_tr) < 0.05 * e_tr, (m, e_box, e_tr)
+    assert all(b < a for a, b in zip(diffs, diffs[1:])), diffs
+    assert diffs[-1] < 0.01
+
+
 # ---------------------------------------------------------------------------
 # Source encoding (Sec. 3.2, App. E)
 # ---------------------------------------------------------------------------
