@@ -85,6 +85,11 @@ typedef struct fwi_problem {
   int32_t sims_per_launch;  /* 0: all simulations of a phase share each launch
                                (K shots, adjoint and TR together); 1: the plain form,
                                one simulation per launch sequence                    */
+  int32_t per_shot_models;  /* 0: one sound-speed model per call, the gradient is the
+                               mean over the K super-shots; 1: super-shot k is an
+                               instance of its own -- model c + k N in, gradient
+                               grad + k N out (c and grad are [K][N]) -- so instances
+                               that share grid and transducers share every launch    */
 } fwi_problem;
 
 typedef struct fwi_plan fwi_plan;
@@ -110,8 +115,28 @@ fwi_status fwi_plan_create(const fwi_problem *prob, size_t *workspace_bytes, fwi
 fwi_status fwi_plan_bind_workspace(fwi_plan *plan, void *dev_ptr, size_t bytes);
 
 /*
+ * Time-reversal re-simulation on a box enclosing Gamma (Sec. 3.1: the TR simulation
+ * domain only needs to enclose Gamma).  After this call, fwi_gradient runs its TR
+ * simulations on the box [origin, origin + size) of the grid, a grid of its own with the
+ * same dx, dt and c_ref, its own PML of pml[a] cells inside the box (same profile rule and
+ * pml_alpha as the plan), and c0 cropped from the model given to each call; the adjoint
+ * simulations stay on the whole grid.  The boundary history and the Gamma values are
+ * shared, so the gradient keeps its layout.  Forward calls are unchanged.
+ *   origin, size, pml: host [3] (x, y, z) in cells; size is the box's FFT grid (each a
+ *                product of 2, 3, 5); every Gamma voxel must lie inside the box and
+ *                outside its PML.
+ *   workspace_bytes: out, the plan's new workspace size (the box plan's workspace and
+ *                the cropped c0 added, the whole-grid TR simulations removed).
+ * Must be called before fwi_plan_bind_workspace; calling it again replaces the box.
+ * Errors: FWI_EINVAL (bound plan, box outside the grid, Gamma outside the box interior),
+ * FWI_ENOTSUP (box size not supported), FWI_ENOMEM.
+ */
+fwi_status fwi_plan_set_tr_box(fwi_plan *plan, const int32_t origin[3], const int32_t size[3],
+                               const int32_t pml[3], size_t *workspace_bytes);
+
+/*
  * Forward simulations of K encoded super-shots (Alg. 1, forward loop).
- *   c:       device [nx*ny*nz] sound speed c0 [m/s]
+ *   c:       device [nx*ny*nz] sound speed c0 [m/s] ([K][nx*ny*nz] with per_shot_models)
  *   weights: device [K][n_src] encoding weights w (Sec. 3.2), e.g. Rademacher +-1
  *   traces:  device out [K][nt][n_rec], f^n = M p after iteration n
  * Errors: FWI_EINVAL (K outside 1..max_shots, NULL pointer), FWI_ECUDA.
@@ -122,13 +147,14 @@ fwi_status fwi_forward(fwi_plan *plan, const float *c, const float *weights, int
 /*
  * Misfit and sound-speed gradient, averaged over K encoded super-shots
  * (Alg. 1 whole; mean of independent estimates, Sec. 4.5).
- *   c:        device [N] sound speed
+ *   c:        device [N] sound speed ([K][N], one model per super-shot, with per_shot_models)
  *   weights:  device [K][n_src]
  *   observed: device observed data; observed_encoded = 1: [K][nt][n_rec], already
  *             encoded as f_hat = sum_i w_i f_i; observed_encoded = 0: raw per-source
  *             data [n_src][nt][n_rec], encoded on the device with `weights`.
  *   misfit:   device out [K] FP64, D_k = 0.5 ||q_k||^2
- *   grad:     device out [N] FP64, (1/K) sum_k of the gradient on Gamma, 0 elsewhere
+ *   grad:     device out [N] FP64, (1/K) sum_k of the gradient on Gamma, 0 elsewhere;
+ *             with per_shot_models [K][N], the gradient of each super-shot alone
  *   traces:   device out [K][nt][n_rec] simulated traces, or NULL
  * Errors: FWI_EINVAL, FWI_ECUDA.
  */
@@ -238,10 +264,13 @@ fwi_status fwi_resampler_destroy(fwi_resampler *resampler);
  */
 fwi_status fwi_plan_status(fwi_plan *plan);
 
-/* Voxel-steps one call performs: (forward + TR + adjoint iterations) * voxels * K. */
+/* Voxel-steps one call performs: (forward + adjoint iterations) * voxels * K, plus TR
+ * iterations * (box or grid) voxels * K for a gradient. */
 int64_t fwi_plan_voxel_steps(const fwi_plan *plan, int32_t K, int32_t gradient);
 
-/* Number of kernel launches one call issues (for launch accounting). */
+/* Number of kernel launches one fwi_forward (gradient = 0) or fwi_gradient (1) call
+ * with encoded observed data issues under the plan's current schedule (for launch
+ * accounting; raw observed data add one encoding launch). */
 int64_t fwi_plan_launches(const fwi_plan *plan, int32_t K, int32_t gradient);
 
 /*
@@ -289,7 +318,9 @@ typedef enum fwi_kernel {
  * Profiling hook: with enable = 1, every later launch of a kernel whose bit is
  * set in `kernel_mask` (bit k = fwi_kernel k) is bracketed by CUDA events on
  * its stream; at most `capacity` launches are kept, later ones are not timed.
- * enable = 0 stops recording and keeps the totals.  Host-side event objects
+ * enable = 0 stops recording and keeps the totals.  Launches issued into a stream
+ * that is being captured (a batch graph, a serving graph) are not timed: an event
+ * recorded during capture is only a graph dependency.  Host-side event objects
  * only; no device memory is allocated.  Errors: FWI_EINVAL, FWI_ECUDA.
  */
 fwi_status fwi_plan_profile(fwi_plan *plan, int32_t kernel_mask, int32_t enable, int32_t capacity);
@@ -336,7 +367,10 @@ fwi_status fwi_adjoint_source_noalloc(const float *traces, const float *observed
  * The first fwi_batch_gradient call with a given set of arguments captures every
  * plan's launch sequence into one graph, one stream branch per plan, so the
  * instances overlap on the GPU; later calls with identical arguments replay it
- * (any change of pointer or K re-captures).  Plans must not be used elsewhere
+ * (any change of pointer or K, and any fwi_plan_bind_workspace or
+ * fwi_plan_set_schedule on a member plan since the capture, re-captures).  The
+ * output pointers are part of the key: callers that want replays pass the same
+ * misfit and grad buffers on every call.  Plans must not be used elsewhere
  * while a batch that contains them runs.  Results are identical to n separate
  * fwi_gradient calls.  Errors: FWI_EINVAL, FWI_ECUDA.
  */

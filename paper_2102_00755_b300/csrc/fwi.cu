@@ -63,12 +63,14 @@ __global__ void k_prepare_coefs(const float* __restrict__ c, double dt, double d
 // amp[k][n][u] = coef_u * (sum_{i at u} w[k][i]) * s(t_n): the encoded source (Sec. 3.2)
 // delay (optional, [K][n_src] whole time steps, Eq. 13): emitter i of super-shot k
 // emits s(t_n - delay dt), zero outside the wavelet's samples
-__global__ void k_source_amp(const float* __restrict__ w, int n_src, const float* __restrict__ coef,
+// coef: [models][n_us], shot k uses model k when per_model, else model 0
+__global__ void k_source_amp(const float* __restrict__ w, int n_src, const float* __restrict__ coef0,
                              const int* mptr, const int* mem, int n_us, const float* __restrict__ wav,
-                             int nt, const int* __restrict__ delay, float* __restrict__ amp) {
+                             int nt, const int* __restrict__ delay, float* __restrict__ amp, int per_model) {
   const int n = blockIdx.x;
   const int k = blockIdx.y;
   const float s = wav[n];
+  const float* coef = coef0 + (per_model ? (size_t)k * n_us : 0);
   for (int u = threadIdx.x; u < n_us; u += blockDim.x) {
     float ws = 0.f;
     for (int e = mptr[u]; e < mptr[u + 1]; ++e) {
@@ -159,26 +161,49 @@ __global__ void k_misfit_final(const double* dpart, int nblk, int K, double* mis
   }
 }
 
-// grad_k(Gamma) += 2/(dt c0^3) (p+ - 2 p0 + p-) p_adj  (FP64 accumulator, Alg. 1)
+// grad_k(Gamma) += 2/(dt c0^3) (p+ - 2 p0 + p-) p_adj  (Alg. 1; second difference, product
+// and accumulator in FP64).  The two-step mass kernels do the same inside the next
+// iteration's adjoint launch; this kernel serves the other kernel families and the
+// last iteration.
 __global__ void k_accumulate(const float* __restrict__ ring, const float* __restrict__ pa,
-                             const float* __restrict__ coefG, int n_gamma, int sa, int sb, int sc,
-                             double* __restrict__ acc, const int* bad, int k0) {
+                             const float* __restrict__ coefG0, int n_gamma, int sa, int sb, int sc,
+                             double* __restrict__ acc, const int* bad, int k0, int per_model) {
   if (*bad) return;
   const int k = k0 + blockIdx.y;
-  const float* rk = ring + (size_t)k * 3 * n_gamma;
+  const float* coefG = coefG0 + (per_model ? (size_t)k * n_gamma : 0);
+  const float* rk = ring + (size_t)k * kRing * n_gamma;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_gamma; j += gridDim.x * blockDim.x) {
-    const float d2 = rk[(size_t)sa * n_gamma + j] - 2.f * rk[(size_t)sb * n_gamma + j] +
-                     rk[(size_t)sc * n_gamma + j];
-    acc[(size_t)k * n_gamma + j] += (double)(coefG[j] * d2 * pa[(size_t)k * n_gamma + j]);
+    const double d2 = (double)rk[(size_t)sa * n_gamma + j] - 2.0 * (double)rk[(size_t)sb * n_gamma + j] +
+                      (double)rk[(size_t)sc * n_gamma + j];
+    acc[(size_t)k * n_gamma + j] += (double)coefG[j] * d2 * (double)pa[(size_t)k * n_gamma + j];
   }
 }
 
+// grad = scale * mean_k acc_k on Gamma; with each_shot, grad[k] = scale * acc_k (one
+// gradient per super-shot, [K][nvox])
 __global__ void k_grad_final(const double* __restrict__ acc, const int* __restrict__ gam_idx,
-                             int n_gamma, int K, double scale, double* __restrict__ grad) {
+                             int n_gamma, int K, double scale, double* __restrict__ grad, int each_shot,
+                             int64_t nvox) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_gamma; j += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < K; ++k) s += acc[(size_t)k * n_gamma + j];
-    grad[gam_idx[j]] = scale * s / K;
+    if (each_shot) {
+      for (int k = 0; k < K; ++k) grad[(size_t)k * nvox + gam_idx[j]] = scale * acc[(size_t)k * n_gamma + j];
+    } else {
+      double s = 0.0;
+      for (int k = 0; k < K; ++k) s += acc[(size_t)k * n_gamma + j];
+      grad[gam_idx[j]] = scale * s / K;
+    }
+  }
+}
+
+// c0 of the TR box (Sec. 3.1): cb[x + nxb (y + nyb z)] = c[(x0 + x) + nx ((y0 + y) + ny (z0 + z))]
+__global__ void k_crop(const float* __restrict__ c, int nx, int ny, int x0, int y0, int z0, int nxb, int nyb,
+                       int nzb, float* __restrict__ cb) {
+  const int64_t n = (int64_t)nxb * nyb * nzb;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nxb);
+    const int64_t r = i / nxb;
+    const int y = (int)(r % nyb), z = (int)(r / nyb);
+    cb[i] = c[((int64_t)(z + z0) * ny + (y + y0)) * nx + (x + x0)];
   }
 }
 
@@ -327,6 +352,17 @@ struct fwi_plan {
   int nblk_misfit;
   char* ws = nullptr;
   size_t ws_bytes = 0;
+  // bumped by every workspace binding and schedule change: a batch graph captured
+  // before the change holds stale pointers or launch shapes and must be re-captured
+  uint64_t generation = 0;
+  // TR re-simulation on a box enclosing Gamma (Sec. 3.1): a plan of the box's grid that
+  // runs only TR simulations, with its workspace and the cropped sound speed inside
+  // this plan's workspace.  tr_only marks such a box plan.
+  fwi_plan* tr = nullptr;
+  bool tr_only = false;
+  int models = 1;       // sound-speed models: K when each super-shot has its own, else 1
+  int tr_origin[3] = {0, 0, 0};
+  size_t o_trc = 0, o_trws = 0;
   cudaStream_t last = nullptr;
   bool used = false;
   // extra streams of the stream-group form, with the fork event and one join event each
@@ -356,6 +392,7 @@ void sim_ptrs(fwi_plan* p, int s, SimPtrs* out, int role, int shot) {
   }
   out->role = role;
   out->shot = shot;
+  out->model = p->models > 1 ? shot : 0;
 }
 
 void base_params(fwi_plan* p, StepParams* P) {
@@ -404,6 +441,8 @@ void base_params(fwi_plan* p, StepParams* P) {
   P->gam_ptr = at<int>(p, p->o_gam_ptr); P->gam_pf = at<int>(p, p->o_gam_pf);
   P->pa = at<float>(p, p->o_pa);
   P->ring = at<float>(p, p->o_ring);
+  P->acc = at<double>(p, p->o_acc);
+  P->coefG = at<float>(p, p->o_coefG);
 }
 
 thread_local char g_last_cuda_error[256] = "";
@@ -522,11 +561,16 @@ void set_attrs(fwi_plan* p) {
   cudaFuncGetAttributes(&a, k_misfit_final);
   cudaFuncGetAttributes(&a, k_accumulate);
   cudaFuncGetAttributes(&a, k_grad_final);
+  cudaFuncGetAttributes(&a, k_crop);
 }
 
 void prof_begin(fwi_plan* p, int kernel, cudaStream_t st, int nsims, int* slot) {
   *slot = -1;
   if (!p->prof_on || !((p->prof_mask >> kernel) & 1)) return;
+  // an event recorded into a stream capture becomes a graph dependency, not a
+  // timestamp: launches issued while the stream is being captured are not timed
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
   if (2 * (p->prof_used + 1) > (int)p->prof_ev.size()) return;
   *slot = p->prof_used++;
   p->prof_kind[*slot] = kernel;
@@ -754,19 +798,29 @@ fwi_status zero_sim(fwi_plan* p, int s, cudaStream_t st) {
 }
 
 // common per-call preparation: c^2, range flag, sparse coefficients
+// c: [models][nvox], one model per super-shot when the plan has per-shot models
 fwi_status prepare(fwi_plan* p, const float* c, cudaStream_t st) {
   const fwi_problem& q = p->prob;
   CK(cudaMemsetAsync(p->ws + p->o_bad, 0, sizeof(int), st));
-  k_prepare_c<<<592, 256, 0, st>>>(c, at<float>(p, p->o_c2), p->nvox, (float)q.c_ref, at<int>(p, p->o_bad));
-  LAUNCHED("k_prepare_c");
-  k_prepare_coefs<<<148, 256, 0, st>>>(c, q.dt, q.dx, at<int>(p, p->o_us_vox), p->n_us,
-                                       at<float>(p, p->o_us_coef), at<int>(p, p->o_ur_vox), p->n_ur,
-                                       at<float>(p, p->o_ur_coef), at<int>(p, p->o_gam_vox), q.n_gamma,
-                                       at<float>(p, p->o_coefG), at<int>(p, p->o_lay_vox), q.n_layer,
-                                       at<float>(p, p->o_inv3c2));
-  LAUNCHED("k_prepare_coefs");
+  if (p->tr && p->tr->ws) CK(cudaMemsetAsync(p->tr->ws + p->tr->o_bad, 0, sizeof(int), st));
+  for (int m = 0; m < p->models; ++m) {
+    const float* cm = c + (size_t)m * p->nvox;
+    k_prepare_c<<<592, 256, 0, st>>>(cm, at<float>(p, p->o_c2) + (size_t)m * p->nvox, p->nvox, (float)q.c_ref,
+                                     at<int>(p, p->o_bad));
+    LAUNCHED("k_prepare_c");
+    k_prepare_coefs<<<148, 256, 0, st>>>(
+        cm, q.dt, q.dx, at<int>(p, p->o_us_vox), p->n_us, at<float>(p, p->o_us_coef) + (size_t)m * p->n_us,
+        at<int>(p, p->o_ur_vox), p->n_ur, at<float>(p, p->o_ur_coef) + (size_t)m * p->n_ur, at<int>(p, p->o_gam_vox),
+        q.n_gamma, at<float>(p, p->o_coefG) + (size_t)m * q.n_gamma, at<int>(p, p->o_lay_vox), q.n_layer,
+        at<float>(p, p->o_inv3c2) + (size_t)m * q.n_layer);
+    LAUNCHED("k_prepare_coefs");
+  }
   return FWI_OK;
 }
+
+// The two-step mass kernels (whole planes or split planes) carry the deferred Gamma
+// accumulation; the other kernel families leave it to k_accumulate.
+bool fused_accumulation(const fwi_plan* p) { return p->p2 != 0 || p->s2 != 0; }
 
 // Stream groups: shots [g*KG, min(K, (g+1)*KG)) of group g advance on stream g (0 = the
 // caller's stream), forked from and joined to it.
@@ -786,12 +840,39 @@ fwi_status join_groups(fwi_plan* p, int G, cudaStream_t st) {
   return FWI_OK;
 }
 
+// TR initial value (Alg. 1): p(layer) <- g^Nt, ring slot 0 <- p(Gamma), forward XY
+// transform of p, for the K TR simulations of T on plan p's grid
+fwi_status launch_tr_init(fwi_plan* p, const StepParams& T, int K, cudaStream_t st) {
+  const fwi_problem& q = p->prob;
+  if (p->split) {
+    const int warps = kTpbPlane / 32;
+    const dim3 gy((p->hx + kTY - 1) / kTY, q.nz, K);
+    if (p->epl == 8) {
+      const int g = std::max(1, 16 * 8 / p->hx);
+      launch_split<8>(6, dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), p->smem_xmom, st, T);
+      LAUNCHED("k_xpass_tr_init");
+      launch_split<8>(Y_FWD1, gy, p->smem_ypass1, st, T);
+    } else {
+      const int g = std::max(1, 16 * 16 / p->hx);
+      launch_split<16>(6, dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), p->smem_xmom, st, T);
+      LAUNCHED("k_xpass_tr_init");
+      launch_split<16>(Y_FWD1, gy, p->smem_ypass1, st, T);
+    }
+    LAUNCHED("k_ypass<forward x1>");
+  } else {
+    PLANE_DISPATCH(p, (launch_plane<E, F>(2, dim3(q.nz, K), p->smem_plane, st, T)));
+    LAUNCHED("k_tr_init");
+  }
+  return FWI_OK;
+}
+
 fwi_status run_forward(fwi_plan* p, const float* w, const int* delay, int K, bool record_layer,
                        float* traces, cudaStream_t st) {
   const fwi_problem& q = p->prob;
   k_source_amp<<<dim3(q.nt, K), 128, 0, st>>>(w, q.n_src, at<float>(p, p->o_us_coef),
                                               at<int>(p, p->o_us_mptr), at<int>(p, p->o_us_mem), p->n_us,
-                                              at<float>(p, p->o_wav), q.nt, delay, at<float>(p, p->o_amp));
+                                              at<float>(p, p->o_wav), q.nt, delay, at<float>(p, p->o_amp),
+                                              p->models > 1 ? 1 : 0);
   LAUNCHED("k_source_amp");
   StepParams P;
   base_params(p, &P);
@@ -831,6 +912,62 @@ fwi_status check_call(fwi_plan* p, int K) {
   return FWI_OK;
 }
 
+
+// Workspace layout of a plan.  A plan that only runs TR simulations for another plan
+// (tr_only: the TR box of Sec. 3.1) keeps no traces, data, boundary history or
+// accumulators, and K simulation states instead of 2K; a plan with a TR box keeps K
+// (its adjoint simulations) and the box plan's workspace and cropped sound speed.
+void plan_layout(fwi_plan* p) {
+  const fwi_problem& q = p->prob;
+  const int64_t nvox = p->nvox;
+  p->L = Layout();
+  Layout& L = p->L;
+  const int K = p->K, nt = q.nt;
+  const size_t per_call = p->tr_only ? 0 : 1;   // buffers a TR-only plan does not need
+  p->o_tw = L.add(p->tw.size() * sizeof(float2));
+  p->o_kx2 = L.add(p->kx2.size() * 4); p->o_ky2 = L.add(p->ky2.size() * 4); p->o_kz2 = L.add(p->kz2.size() * 4);
+  for (int a = 0; a < 3; ++a) {
+    p->o_ap[a] = L.add(p->ap[a].size() * sizeof(float2));
+    p->o_am[a] = L.add(p->am[a].size() * sizeof(float2));
+    p->o_lam[a] = L.add(p->lam[a].size() * 4);
+    p->o_lams[a] = L.add(p->lams[a].size() * 4);
+  }
+  const size_t nkey = (size_t)q.nz * p->npair + 1;
+  p->o_us_ptr = L.add(nkey * 4); p->o_us_pf = L.add(p->n_us * 4); p->o_us_vox = L.add(p->n_us * 4);
+  p->o_us_mptr = L.add((p->n_us + 1) * 4); p->o_us_mem = L.add(q.n_src * 4);
+  p->o_ur_ptr = L.add(nkey * 4); p->o_ur_pf = L.add(p->n_ur * 4); p->o_ur_vox = L.add(p->n_ur * 4);
+  p->o_ur_mptr = L.add((p->n_ur + 1) * 4); p->o_ur_mem = L.add(q.n_rec * 4);
+  p->o_rr_ptr = L.add(nkey * 4); p->o_rr_pf = L.add(q.n_rec * 4); p->o_rr_col = L.add(q.n_rec * 4);
+  p->o_lay_ptr = L.add(nkey * 4); p->o_lay_vox = L.add((size_t)q.n_layer * 4 + 4);
+  p->o_lay_pf = L.add((size_t)q.n_layer * 4 + 4);
+  p->o_gam_ptr = L.add(nkey * 4); p->o_gam_vox = L.add((size_t)q.n_gamma * 4);
+  p->o_gam_pf = L.add((size_t)q.n_gamma * 4);
+  p->o_wav = L.add((size_t)nt * 4);
+  p->o_bad = L.add(4);
+  const size_t M = p->models;
+  p->o_c2 = L.add(M * nvox * 4);
+  p->o_us_coef = L.add(M * p->n_us * 4); p->o_ur_coef = L.add(M * p->n_ur * 4);
+  p->o_coefG = L.add(M * q.n_gamma * 4); p->o_inv3c2 = L.add(M * q.n_layer * 4 + 4);
+  p->o_amp = L.add(per_call * K * nt * p->n_us * 4);
+  p->o_traces = L.add(per_call * K * nt * q.n_rec * 4);
+  p->o_obs = L.add(per_call * K * nt * q.n_rec * 4);
+  p->o_qf = L.add(per_call * K * nt * q.n_rec * 4);
+  p->o_ghist = L.add(per_call * K * nt * q.n_layer * 4 + 4);
+  p->o_ring = L.add(per_call * K * kRing * q.n_gamma * 4);
+  p->o_pa = L.add(per_call * K * q.n_gamma * 4);
+  p->o_acc = L.add(per_call * K * q.n_gamma * 8);
+  p->nblk_misfit = (q.n_rec + 255) / 256;
+  p->o_dpart = L.add(per_call * K * p->nblk_misfit * 8);
+  p->sim_field = ((size_t)nvox * 4 + 255) & ~size_t(255);
+  p->sim_spec = ((size_t)p->mspec * q.nz * sizeof(float2) + 255) & ~size_t(255);
+  p->sim_bytes = 6 * p->sim_field + 3 * p->sim_spec;
+  p->o_sims = L.add((size_t)((p->tr_only || p->tr) ? 1 : 2) * K * p->sim_bytes);
+  if (p->tr) {
+    p->o_trc = L.add(M * p->tr->nvox * 4);
+    p->o_trws = L.add(p->tr->L.total);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -851,7 +988,11 @@ const char* fwi_status_string(fwi_status s) {
   return "unknown status";
 }
 
-fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi_plan** out) {
+}  // extern "C"
+
+namespace {
+// fwi_plan_create; tr_only = a plan that runs only the TR simulations of another plan
+fwi_status fwi_plan_create_impl(const fwi_problem* prob, bool tr_only, size_t* workspace_bytes, fwi_plan** out) {
   if (!prob || !workspace_bytes || !out) return FWI_EINVAL;
   const fwi_problem& q = *prob;
   if (q.nx < 2 || q.ny < 2 || q.nz < 2 || q.nt < 3 || q.n_src < 1 || q.n_rec < 1 ||
@@ -862,7 +1003,7 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   if (!q.src_idx || !q.rec_idx || !q.gamma_idx || (q.n_layer > 0 && !q.layer_idx) || !q.wavelet)
     return FWI_EINVAL;
   if (q.pairing != FWI_PAIRING_LITERAL && q.pairing != FWI_PAIRING_EXACT) return FWI_EINVAL;
-  if (q.sims_per_launch < 0) return FWI_EINVAL;
+  if (q.sims_per_launch < 0 || (q.per_shot_models != 0 && q.per_shot_models != 1)) return FWI_EINVAL;
   for (int a = 0; a < 3; ++a) {
     const int n = a == 0 ? q.nx : (a == 1 ? q.ny : q.nz);
     if (q.pml[a] < 0 || 2 * q.pml[a] > n) return FWI_EINVAL;
@@ -887,6 +1028,8 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
   fwi_plan* p = new (std::nothrow) fwi_plan();
   if (!p) return FWI_ENOMEM;
   p->prob = q;
+  p->tr_only = tr_only;
+  p->models = q.per_shot_models ? q.max_shots : 1;
   p->prob.src_idx = p->prob.rec_idx = p->prob.layer_idx = p->prob.gamma_idx = nullptr;
   p->prob.wavelet = nullptr;
   p->K = q.max_shots;
@@ -962,49 +1105,17 @@ fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi
     delete p;
     return FWI_ENOTSUP;
   }
-  // workspace layout
-  Layout& L = p->L;
-  const int K = p->K, nt = q.nt;
-  p->o_tw = L.add(p->tw.size() * sizeof(float2));
-  p->o_kx2 = L.add(p->kx2.size() * 4); p->o_ky2 = L.add(p->ky2.size() * 4); p->o_kz2 = L.add(p->kz2.size() * 4);
-  for (int a = 0; a < 3; ++a) {
-    p->o_ap[a] = L.add(p->ap[a].size() * sizeof(float2));
-    p->o_am[a] = L.add(p->am[a].size() * sizeof(float2));
-    p->o_lam[a] = L.add(p->lam[a].size() * 4);
-    p->o_lams[a] = L.add(p->lams[a].size() * 4);
-  }
-  const size_t nkey = (size_t)q.nz * p->npair + 1;
-  p->o_us_ptr = L.add(nkey * 4); p->o_us_pf = L.add(p->n_us * 4); p->o_us_vox = L.add(p->n_us * 4);
-  p->o_us_mptr = L.add((p->n_us + 1) * 4); p->o_us_mem = L.add(q.n_src * 4);
-  p->o_ur_ptr = L.add(nkey * 4); p->o_ur_pf = L.add(p->n_ur * 4); p->o_ur_vox = L.add(p->n_ur * 4);
-  p->o_ur_mptr = L.add((p->n_ur + 1) * 4); p->o_ur_mem = L.add(q.n_rec * 4);
-  p->o_rr_ptr = L.add(nkey * 4); p->o_rr_pf = L.add(q.n_rec * 4); p->o_rr_col = L.add(q.n_rec * 4);
-  p->o_lay_ptr = L.add(nkey * 4); p->o_lay_vox = L.add((size_t)q.n_layer * 4 + 4);
-  p->o_lay_pf = L.add((size_t)q.n_layer * 4 + 4);
-  p->o_gam_ptr = L.add(nkey * 4); p->o_gam_vox = L.add((size_t)q.n_gamma * 4);
-  p->o_gam_pf = L.add((size_t)q.n_gamma * 4);
-  p->o_wav = L.add((size_t)nt * 4);
-  p->o_bad = L.add(4);
-  p->o_c2 = L.add((size_t)nvox * 4);
-  p->o_us_coef = L.add(p->n_us * 4); p->o_ur_coef = L.add(p->n_ur * 4);
-  p->o_coefG = L.add((size_t)q.n_gamma * 4); p->o_inv3c2 = L.add((size_t)q.n_layer * 4 + 4);
-  p->o_amp = L.add((size_t)K * nt * p->n_us * 4);
-  p->o_traces = L.add((size_t)K * nt * q.n_rec * 4);
-  p->o_obs = L.add((size_t)K * nt * q.n_rec * 4);
-  p->o_qf = L.add((size_t)K * nt * q.n_rec * 4);
-  p->o_ghist = L.add((size_t)K * nt * q.n_layer * 4 + 4);
-  p->o_ring = L.add((size_t)K * 3 * q.n_gamma * 4);
-  p->o_pa = L.add((size_t)K * q.n_gamma * 4);
-  p->o_acc = L.add((size_t)K * q.n_gamma * 8);
-  p->nblk_misfit = (q.n_rec + 255) / 256;
-  p->o_dpart = L.add((size_t)K * p->nblk_misfit * 8);
-  p->sim_field = ((size_t)nvox * 4 + 255) & ~size_t(255);
-  p->sim_spec = ((size_t)p->mspec * q.nz * sizeof(float2) + 255) & ~size_t(255);
-  p->sim_bytes = 6 * p->sim_field + 3 * p->sim_spec;
-  p->o_sims = L.add((size_t)2 * K * p->sim_bytes);
-  *workspace_bytes = L.total;
+  plan_layout(p);
+  *workspace_bytes = p->L.total;
   *out = p;
   return FWI_OK;
+}
+}  // namespace
+
+extern "C" {
+
+fwi_status fwi_plan_create(const fwi_problem* prob, size_t* workspace_bytes, fwi_plan** out) {
+  return fwi_plan_create_impl(prob, false, workspace_bytes, out);
 }
 
 fwi_status fwi_plan_bind_workspace(fwi_plan* p, void* dev_ptr, size_t bytes) {
@@ -1012,6 +1123,7 @@ fwi_status fwi_plan_bind_workspace(fwi_plan* p, void* dev_ptr, size_t bytes) {
   if (bytes < p->L.total) return FWI_ENOMEM;
   p->ws = static_cast<char*>(dev_ptr);
   p->ws_bytes = bytes;
+  p->generation++;
   auto up = [&](size_t off, const void* src, size_t n) -> cudaError_t {
     if (n == 0) return cudaSuccess;
     return cudaMemcpy(p->ws + off, src, n, cudaMemcpyHostToDevice);
@@ -1051,6 +1163,10 @@ fwi_status fwi_plan_bind_workspace(fwi_plan* p, void* dev_ptr, size_t bytes) {
   if (!p->ev_fork) CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
   set_attrs(p);
   CK(cudaGetLastError());
+  if (p->tr) {
+    const fwi_status st = fwi_plan_bind_workspace(p->tr, p->ws + p->o_trws, p->tr->L.total);
+    if (st != FWI_OK) return st;
+  }
   return FWI_OK;
 }
 
@@ -1133,78 +1249,96 @@ fwi_status gradient_impl(fwi_plan* p, const float* c, const float* weights, cons
   k_misfit_final<<<1, 32, 0, st>>>(at<double>(p, p->o_dpart), p->nblk_misfit, K, misfit);
   LAUNCHED("k_misfit_final");
   CK(cudaMemsetAsync(p->ws + p->o_acc, 0, (size_t)K * q.n_gamma * 8, st));
-  // adjoint sims 0..K-1 and TR sims K..2K-1
-  StepParams P;
+  // Adjoint simulations 0..K-1 on this plan's grid; TR simulations on the grid of tp:
+  // this plan (simulations K..2K-1) or its TR box (Sec. 3.1; the box plan's simulations
+  // 0..K-1, c0 cropped from the full model, the boundary history and the ring shared).
+  fwi_plan* tp = p->tr ? p->tr : p;
+  if (p->tr) {
+    const fwi_problem& b = tp->prob;
+    for (int m = 0; m < p->models; ++m) {
+      k_crop<<<592, 256, 0, st>>>(c + (size_t)m * p->nvox, q.nx, q.ny, p->tr_origin[0], p->tr_origin[1],
+                                  p->tr_origin[2], b.nx, b.ny, b.nz, at<float>(p, p->o_trc) + (size_t)m * tp->nvox);
+      LAUNCHED("k_crop");
+    }
+    if ((s = prepare(tp, at<float>(p, p->o_trc), st)) != FWI_OK) return s;
+  }
+  StepParams P, T;
   base_params(p, &P);
+  base_params(tp, &T);
+  T.ghist = P.ghist;
+  T.ring = P.ring;
+  const int tr0 = p->tr ? 0 : K;
   for (int k = 0; k < K; ++k) {
     sim_ptrs(p, k, &P.sims[k], ROLE_ADJOINT, k);
-    sim_ptrs(p, K + k, &P.sims[K + k], ROLE_TR, k);
+    sim_ptrs(tp, tr0 + k, &T.sims[k], ROLE_TR, k);
     if ((s = zero_sim(p, k, st)) != FWI_OK) return s;
-    if ((s = zero_sim(p, K + k, st)) != FWI_OK) return s;
+    if ((s = zero_sim(tp, tr0 + k, st)) != FWI_OK) return s;
   }
   // TR initial value and the lead TR step (m = 1)
-  StepParams T = P;
   T.nsims = K;
   for (int k = 0; k < K; ++k) {
-    T.sims[k] = P.sims[K + k];
     T.tidx[k] = 1;
     T.slot[k] = 1;
   }
-  if (p->split) {
-    const int warps = kTpbPlane / 32;
-    const dim3 gy((p->hx + kTY - 1) / kTY, q.nz, K);
-    if (p->epl == 8) {
-      const int g = std::max(1, 16 * 8 / p->hx);
-      launch_split<8>(6, dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), p->smem_xmom, st, T);
-      LAUNCHED("k_xpass_tr_init");
-      launch_split<8>(Y_FWD1, gy, p->smem_ypass1, st, T);
-    } else {
-      const int g = std::max(1, 16 * 16 / p->hx);
-      launch_split<16>(6, dim3((p->npair + warps * g - 1) / (warps * g), q.nz, K), p->smem_xmom, st, T);
-      LAUNCHED("k_xpass_tr_init");
-      launch_split<16>(Y_FWD1, gy, p->smem_ypass1, st, T);
-    }
-    LAUNCHED("k_ypass<forward x1>");
-  } else {
-    PLANE_DISPATCH(p, (launch_plane<E, F>(2, dim3(q.nz, K), p->smem_plane, st, T)));
-    LAUNCHED("k_tr_init");
-  }
-  if ((s = launch_step(p, T, st)) != FWI_OK) return s;
+  if ((s = launch_tr_init(tp, T, K, st)) != FWI_OK) return s;
+  if ((s = launch_step(tp, T, st)) != FWI_OK) return s;
   // interleaved adjoint and TR iterations
   const bool exact = q.pairing == FWI_PAIRING_EXACT;
   const int nit = exact ? Nt + 1 : Nt - 1;
   const int nblk = (q.n_gamma + 255) / 256;
+  // The two-step mass kernels add iteration it's gradient term inside iteration it + 1's
+  // adjoint launch (before they overwrite pa); the last iteration's, and every
+  // iteration's for the other kernel families, runs as k_accumulate.
+  const bool fused = fused_accumulation(p);
+  auto accumulate = [&](int it, int k0, int nk, cudaStream_t gs) -> fwi_status {
+    k_accumulate<<<dim3(nblk, nk), 256, 0, gs>>>(at<float>(p, p->o_ring), at<float>(p, p->o_pa),
+                                                 at<float>(p, p->o_coefG), q.n_gamma, it % kRing,
+                                                 (it + 1) % kRing, (it + 2) % kRing, at<double>(p, p->o_acc),
+                                                 at<int>(p, p->o_bad), k0, p->models > 1 ? 1 : 0);
+    LAUNCHED("k_accumulate");
+    return FWI_OK;
+  };
   // shots [k0, k0 + nk) advance on stream gs: their adjoint simulations (k) and TR
   // simulations (K + k) in one launch sequence, then their Gamma accumulation
   auto iterate = [&](int it, int k0, int nk, cudaStream_t gs) -> fwi_status {
     const int qi = exact ? it : it + 1;    // row of Q injected by this adjoint step
     const int m = it + 2;                  // TR state produced in this iteration
-    const int slot = m % 3;
+    const int slot = m % kRing;
     StepParams S = P;
     S.nsims = nk;
     for (int k = 0; k < nk; ++k) {
       S.sims[k] = P.sims[k0 + k];
       S.tidx[k] = qi;
     }
-    if (m <= Nt) {
+    if (fused && it > 0) {
+      S.acc_prev = 1;
+      S.acc_slot[0] = (it - 1) % kRing;
+      S.acc_slot[1] = it % kRing;
+      S.acc_slot[2] = (it + 1) % kRing;
+    }
+    StepParams R = T;                      // TR simulations of these shots
+    R.nsims = nk;
+    for (int k = 0; k < nk; ++k) {
+      R.sims[k] = T.sims[k0 + k];
+      R.tidx[k] = m;
+      R.slot[k] = slot;
+    }
+    if (m <= Nt && !p->tr) {               // adjoint and TR simulations share each launch
       S.nsims = 2 * nk;
       for (int k = 0; k < nk; ++k) {
-        S.sims[nk + k] = P.sims[K + k0 + k];
+        S.sims[nk + k] = R.sims[k];
         S.tidx[nk + k] = m;
         S.slot[nk + k] = slot;
       }
-    } else {
+    } else if (m > Nt) {
       for (int k = k0; k < k0 + nk; ++k)
-        CK(cudaMemsetAsync(at<float>(p, p->o_ring) + ((size_t)k * 3 + slot) * q.n_gamma, 0,
+        CK(cudaMemsetAsync(at<float>(p, p->o_ring) + ((size_t)k * kRing + slot) * q.n_gamma, 0,
                            (size_t)q.n_gamma * 4, gs));
     }
     fwi_status r = launch_step(p, S, gs);
     if (r != FWI_OK) return r;
-    k_accumulate<<<dim3(nblk, nk), 256, 0, gs>>>(at<float>(p, p->o_ring), at<float>(p, p->o_pa),
-                                                 at<float>(p, p->o_coefG), q.n_gamma, it % 3, (it + 1) % 3,
-                                                 (it + 2) % 3, at<double>(p, p->o_acc), at<int>(p, p->o_bad), k0);
-    LAUNCHED("k_accumulate");
-    return FWI_OK;
+    if (m <= Nt && p->tr && (r = launch_step(tp, R, gs)) != FWI_OK) return r;
+    return fused ? FWI_OK : accumulate(it, k0, nk, gs);
   };
   const int G = group_count(p, K), KG = (K + G - 1) / G;
   if ((s = fork_groups(p, G, st)) != FWI_OK) return s;
@@ -1214,12 +1348,19 @@ fwi_status gradient_impl(fwi_plan* p, const float* c, const float* weights, cons
       if (nk > 0 && (s = iterate(it, k0, nk, group_stream(p, g, st))) != FWI_OK) return s;
     }
   }
+  if (fused) {
+    for (int g = 0; g < G; ++g) {
+      const int k0 = g * KG, nk = std::min(K, k0 + KG) - k0;
+      if (nk > 0 && (s = accumulate(nit - 1, k0, nk, group_stream(p, g, st))) != FWI_OK) return s;
+    }
+  }
   if ((s = join_groups(p, G, st)) != FWI_OK) return s;
   // mean over shots, scaled to dD/dc if requested
   const double scale = q.c_rec > 0 ? q.dx * q.c_rec / 2.0 : 1.0;
-  CK(cudaMemsetAsync(grad, 0, (size_t)p->nvox * 8, st));
+  const int each = p->models > 1 ? 1 : 0;            // one gradient per super-shot
+  CK(cudaMemsetAsync(grad, 0, (size_t)(each ? K : 1) * p->nvox * 8, st));
   k_grad_final<<<(q.n_gamma + 255) / 256, 256, 0, st>>>(at<double>(p, p->o_acc), at<int>(p, p->o_gam_vox),
-                                                        q.n_gamma, K, scale, grad);
+                                                        q.n_gamma, K, scale, grad, each, p->nvox);
   LAUNCHED("k_grad_final");
   if (traces)
     CK(cudaMemcpyAsync(traces, p->ws + p->o_traces, (size_t)K * nt * q.n_rec * 4,
@@ -1235,6 +1376,8 @@ fwi_status fwi_plan_status(fwi_plan* p) {
   CK(cudaStreamSynchronize(p->last));
   int bad = 0;
   CK(cudaMemcpy(&bad, p->ws + p->o_bad, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!bad && p->tr)                         // the TR box plan keeps its own flag
+    CK(cudaMemcpy(&bad, p->tr->ws + p->tr->o_bad, sizeof(int), cudaMemcpyDeviceToHost));
   return bad ? FWI_EUNSTABLE : FWI_OK;
 }
 
@@ -1242,26 +1385,45 @@ int64_t fwi_plan_voxel_steps(const fwi_plan* p, int32_t K, int32_t gradient) {
   if (!p) return -1;
   const int64_t nt = p->prob.nt, Nt = nt - 1;
   int64_t steps = nt;
+  int64_t tr = 0;
   if (gradient) {
     const bool exact = p->prob.pairing == FWI_PAIRING_EXACT;
-    steps += Nt;                                   // TR: lead step + loop steps with m <= Nt
+    tr = Nt;                                       // TR: lead step + loop steps with m <= Nt
     steps += exact ? Nt + 1 : Nt - 1;              // adjoint
   }
-  return steps * p->nvox * K;
+  return (steps * p->nvox + tr * (p->tr ? p->tr->nvox : p->nvox)) * K;
 }
 
 int64_t fwi_plan_launches(const fwi_plan* p, int32_t K, int32_t gradient) {
   if (!p || K < 1) return -1;
   const int64_t nt = p->prob.nt, Nt = nt - 1;
   const int spl = p->prob.sims_per_launch;
-  auto seqs = [&](int nsims) -> int64_t { return (spl <= 0 || spl >= nsims) ? 1 : (nsims + spl - 1) / spl; };
-  int64_t n = 2 + 1 + 4 * nt * seqs(K);                 // prepare x2, source amplitudes, steps
+  // kernel launches of one time step over nsims simulations on plan q's grid
+  auto step = [&](const fwi_plan* q, int nsims) -> int64_t {
+    const int64_t seqs = (spl <= 0 || spl >= nsims) ? 1 : (nsims + spl - 1) / spl;
+    return (q->split ? 8 : 4) * seqs;
+  };
+  const fwi_plan* tp = p->tr ? p->tr : p;
+  const int G = group_count(p, K), KG = (K + G - 1) / G;
+  int64_t n = 2 + 1;                                    // prepare x2, source amplitudes
+  for (int g = 0; g < G; ++g) {                         // forward steps (groups with shots)
+    const int ng = std::min(K, (g + 1) * KG) - g * KG;
+    if (ng > 0) n += nt * step(p, ng);
+  }
   if (gradient) {
     const bool exact = p->prob.pairing == FWI_PAIRING_EXACT;
     const int64_t nit = exact ? Nt + 1 : Nt - 1;
-    n += 2 + 1 + 4 * seqs(K);                           // misfit x2, TR init, lead TR step
+    if (p->tr) n += 1 + 2;                              // crop, prepare of the box
+    n += 2 + (tp->split ? 2 : 1) + step(tp, K);         // misfit x2, TR init, lead TR step
     const int64_t full = std::min<int64_t>(nit, Nt - 1);  // iterations with a TR step
-    n += full * (4 * seqs(2 * K) + 1) + (nit - full) * (4 * seqs(K) + 1);
+    const int64_t acc = fused_accumulation(p) ? 0 : 1;  // k_accumulate per iteration
+    for (int g = 0; g < G; ++g) {
+      const int ng = std::min(K, (g + 1) * KG) - g * KG;
+      if (ng <= 0) continue;
+      const int64_t with_tr = p->tr ? step(p, ng) + step(tp, ng) : step(p, 2 * ng);
+      n += full * (with_tr + acc) + (nit - full) * (step(p, ng) + acc);
+      if (!acc) n += 1;                                 // last iteration's accumulation
+    }
     n += 1;                                             // gradient scatter
   }
   return n;
@@ -1388,7 +1550,8 @@ fwi_status fwi_batch_gradient(fwi_batch* b, const float* const* c, const float* 
     fwi_status s = check_call(b->plans[i], K[i]);
     if (s != FWI_OK) return s;
     key.insert(key.end(), {(uintptr_t)c[i], (uintptr_t)w[i], (uintptr_t)K[i], (uintptr_t)observed[i],
-                           (uintptr_t)observed_encoded[i], (uintptr_t)misfit[i], (uintptr_t)grad[i]});
+                           (uintptr_t)observed_encoded[i], (uintptr_t)misfit[i], (uintptr_t)grad[i],
+                           (uintptr_t)b->plans[i]->generation});
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!b->exec || key != b->key) {
@@ -1461,6 +1624,7 @@ fwi_status fwi_plan_set_schedule(fwi_plan* p, const fwi_schedule* sc) {
     apply_schedule(p);
     return FWI_ENOTSUP;
   }
+  p->generation++;
   if (p->ws) set_attrs(p);
   return FWI_OK;
 }
@@ -1471,8 +1635,54 @@ fwi_status fwi_plan_get_schedule(const fwi_plan* p, fwi_schedule* sc) {
   return FWI_OK;
 }
 
+fwi_status fwi_plan_set_tr_box(fwi_plan* p, const int32_t origin[3], const int32_t size[3], const int32_t pml[3],
+                               size_t* workspace_bytes) {
+  if (!p || !origin || !size || !pml || !workspace_bytes || p->ws || p->tr_only) return FWI_EINVAL;
+  const fwi_problem& q = p->prob;
+  const int n[3] = {q.nx, q.ny, q.nz};
+  for (int a = 0; a < 3; ++a)
+    if (origin[a] < 0 || size[a] < 2 || origin[a] + size[a] > n[a] || pml[a] < 0 || 2 * pml[a] > size[a])
+      return FWI_EINVAL;
+  // Gamma and the boundary layer in box coordinates (cropping keeps their order); every
+  // Gamma voxel must lie inside the box and outside the box's PML
+  auto to_box = [&](int v, int32_t* out) {
+    const int x = v % q.nx, y = (v / q.nx) % q.ny, z = v / (q.nx * q.ny);
+    const int c[3] = {x - origin[0], y - origin[1], z - origin[2]};
+    for (int a = 0; a < 3; ++a)
+      if (c[a] < pml[a] || c[a] > size[a] - 1 - pml[a]) return false;
+    *out = c[0] + size[0] * (c[1] + size[1] * c[2]);
+    return true;
+  };
+  std::vector<int32_t> gam(q.n_gamma), lay(q.n_layer);
+  for (int j = 0; j < q.n_gamma; ++j)
+    if (!to_box(p->gam.vox[j], &gam[j])) return FWI_EINVAL;
+  for (int j = 0; j < q.n_layer; ++j)
+    if (!to_box(p->lay.vox[j], &lay[j])) return FWI_EINVAL;
+  fwi_problem b = q;
+  b.nx = size[0]; b.ny = size[1]; b.nz = size[2];
+  for (int a = 0; a < 3; ++a) b.pml[a] = pml[a];
+  // the box plan runs no forward or adjoint simulation: one placeholder transducer each
+  const int32_t none = 0;
+  b.n_src = b.n_rec = 1;
+  b.src_idx = b.rec_idx = &none;
+  b.gamma_idx = gam.data();
+  b.layer_idx = lay.data();
+  b.wavelet = p->wavelet.data();
+  size_t sub_bytes = 0;
+  fwi_plan* sub = nullptr;
+  const fwi_status st = fwi_plan_create_impl(&b, true, &sub_bytes, &sub);
+  if (st != FWI_OK) return st;
+  if (p->tr) fwi_plan_destroy(p->tr);
+  p->tr = sub;
+  for (int a = 0; a < 3; ++a) p->tr_origin[a] = origin[a];
+  plan_layout(p);
+  *workspace_bytes = p->L.total;
+  return FWI_OK;
+}
+
 fwi_status fwi_plan_destroy(fwi_plan* p) {
   if (p) {
+    if (p->tr) fwi_plan_destroy(p->tr);
     for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
     for (int g = 0; g < fwi_plan::kMaxGroups - 1; ++g) {
       if (p->side[g]) cudaStreamDestroy(p->side[g]);

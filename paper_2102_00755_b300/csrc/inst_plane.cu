@@ -13,9 +13,9 @@ void launch_plane(int kind, dim3 g, size_t smem, cudaStream_t st, const StepPara
 
 template <int E, int F>
 void attrs_plane(int cap) {
-  cudaFuncSetAttribute(k_plane_mom<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_plane_mass<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_tr_init<E, F, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  set_smem_cap(k_plane_mom<E, F, F>, cap);
+  set_smem_cap(k_plane_mass<E, F, F>, cap);
+  set_smem_cap(k_tr_init<E, F, F>, cap);
 }
 
 template void launch_plane<FWI_E, FWI_N>(int, dim3, size_t, cudaStream_t, const StepParams&);

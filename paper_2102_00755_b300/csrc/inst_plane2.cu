@@ -12,8 +12,8 @@ void launch_plane2(int kind, dim3 g, size_t smem, cudaStream_t st, const StepPar
 
 template <int N>
 void attrs_plane2(int cap) {
-  cudaFuncSetAttribute(k_plane2_mom<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_plane2_mass<N, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  set_smem_cap(k_plane2_mom<N, N>, cap);
+  set_smem_cap(k_plane2_mass<N, N>, cap);
 }
 
 template void launch_plane2<FWI_N>(int, dim3, size_t, cudaStream_t, const StepParams&);

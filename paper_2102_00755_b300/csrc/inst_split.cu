@@ -18,13 +18,13 @@ void launch_split(int kind, dim3 g, size_t smem, cudaStream_t st, const StepPara
 
 template <int E>
 void attrs_split(int cap) {
-  cudaFuncSetAttribute(k_ypass<Y_INV_MOM, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass<Y_INV_MASS, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass<Y_FWD3, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass<Y_FWD1, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass_mom<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass_mass<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass_tr_init<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  set_smem_cap(k_ypass<Y_INV_MOM, E>, cap);
+  set_smem_cap(k_ypass<Y_INV_MASS, E>, cap);
+  set_smem_cap(k_ypass<Y_FWD3, E>, cap);
+  set_smem_cap(k_ypass<Y_FWD1, E>, cap);
+  set_smem_cap(k_xpass_mom<E>, cap);
+  set_smem_cap(k_xpass_mass<E>, cap);
+  set_smem_cap(k_xpass_tr_init<E>, cap);
 }
 
 template void launch_split<FWI_E>(int, dim3, size_t, cudaStream_t, const StepParams&);

@@ -21,12 +21,12 @@ void launch_split2(int kind, dim3 g, size_t smem, cudaStream_t st, const StepPar
 template <int N>
 void attrs_split2(int cap) {
   constexpr int TY = ty2_for(N), NPC = npc2_for(N);
-  cudaFuncSetAttribute(k_ypass2<Y_INV_MOM, N, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass2<Y_INV_MASS, N, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass2<Y_FWD3, N, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_ypass2<Y_FWD1, N, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass2_mom<N, NPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_xpass2_mass<N, NPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  set_smem_cap(k_ypass2<Y_INV_MOM, N, TY>, cap);
+  set_smem_cap(k_ypass2<Y_INV_MASS, N, TY>, cap);
+  set_smem_cap(k_ypass2<Y_FWD3, N, TY>, cap);
+  set_smem_cap(k_ypass2<Y_FWD1, N, TY>, cap);
+  set_smem_cap(k_xpass2_mom<N, NPC>, cap);
+  set_smem_cap(k_xpass2_mass<N, NPC>, cap);
 }
 
 template void launch_split2<FWI_N>(int, dim3, size_t, cudaStream_t, const StepParams&);

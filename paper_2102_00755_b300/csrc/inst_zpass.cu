@@ -17,10 +17,10 @@ void launch_zpass(int mode, int tz, dim3 g, size_t smem, cudaStream_t st, const 
 
 template <int E, int FZ>
 void attrs_zpass(int cap) {
-  cudaFuncSetAttribute(k_zpass<0, E, FZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_zpass<1, E, FZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_zpass<0, E, FZ, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_zpass<1, E, FZ, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  set_smem_cap(k_zpass<0, E, FZ, 32>, cap);
+  set_smem_cap(k_zpass<1, E, FZ, 32>, cap);
+  set_smem_cap(k_zpass<0, E, FZ, 16>, cap);
+  set_smem_cap(k_zpass<1, E, FZ, 16>, cap);
 }
 
 template void launch_zpass<FWI_E, FWI_N>(int, int, dim3, size_t, cudaStream_t, const StepParams&);

@@ -17,10 +17,10 @@ void launch_zpass2(int mode, int tz, dim3 g, size_t smem, cudaStream_t st, const
 
 template <int NZ>
 void attrs_zpass2(int cap) {
-  cudaFuncSetAttribute(k_zpass2<0, NZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_zpass2<1, NZ, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_zpass2<0, NZ, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-  cudaFuncSetAttribute(k_zpass2<1, NZ, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  set_smem_cap(k_zpass2<0, NZ, 32>, cap);
+  set_smem_cap(k_zpass2<1, NZ, 32>, cap);
+  set_smem_cap(k_zpass2<0, NZ, 16>, cap);
+  set_smem_cap(k_zpass2<1, NZ, 16>, cap);
 }
 
 template void launch_zpass2<FWI_N>(int, int, dim3, size_t, cudaStream_t, const StepParams&);

@@ -41,12 +41,18 @@ constexpr int kTpbZ = 256;
 
 enum Role : int { ROLE_FORWARD = 0, ROLE_ADJOINT = 1, ROLE_TR = 2 };
 
+// Slots of the ring that holds the TR pressure on Gamma, P(m) in slot m % kRing.  The
+// accumulation of an iteration reads P(it), P(it+1), P(it+2) while the same launch's TR
+// simulations of the next iteration write P(it+3): four slots keep them apart.
+constexpr int kRing = 4;
+
 struct SimPtrs {
   float* v[3];
   float* rho[3];
   float2* spec[3];
   int role;
   int shot;
+  int model;           // sound-speed model of this simulation (0 unless each shot has its own)
 };
 
 // Everything a step launch needs; passed by value as a __grid_constant__.
@@ -94,14 +100,36 @@ struct StepParams {
   const float* inv3c2;                                     // [n_layer] 1/(3 c0^2)
   const int* gam_ptr; const int* gam_pf;                   // Gamma (sorted)
   float* pa;                                               // [K][n_gamma] adjoint p on Gamma
-  float* ring;                                             // [K][3][n_gamma] TR p on Gamma
+  float* ring;                                             // [K][kRing][n_gamma] TR p on Gamma
   int record_layer;                                        // forward: record the layer
+  // Gradient accumulation of the previous iteration, done by the adjoint-role mass
+  // kernel before it overwrites pa (two-step kernels only): acc[k][j] += coefG[j]
+  // (P(s0) - 2 P(s1) + P(s2))[j] pa_old[k][j] in FP64, ring slots acc_slot[0..2].
+  double* acc;                                             // [K][n_gamma]
+  const float* coefG;                                      // [n_gamma] 2 / (dt c0^3)
+  int acc_prev;                                            // 1: accumulate before writing pa
+  int acc_slot[3];
   // batch
   int nsims;
   SimPtrs sims[kMaxSims];
   int tidx[kMaxSims];   // forward: n; adjoint: row of Q injected; TR: m (uses g[Nt-m])
   int slot[kMaxSims];   // TR: ring slot written
 };
+
+// Per-model arrays ([models][n], contiguous; one model unless each super-shot has its own):
+// c0^2 on the grid and the sound-speed dependent coefficients at the sparse voxels.
+__device__ __forceinline__ const float* c2_of(const StepParams& P, const SimPtrs& Q) {
+  return P.c2 + (size_t)Q.model * P.nvox;
+}
+__device__ __forceinline__ const float* ur_coef_of(const StepParams& P, const SimPtrs& Q) {
+  return P.ur_coef + (size_t)Q.model * P.n_ur;
+}
+__device__ __forceinline__ const float* inv3c2_of(const StepParams& P, const SimPtrs& Q) {
+  return P.inv3c2 + (size_t)Q.model * P.n_layer;
+}
+__device__ __forceinline__ const float* coefG_of(const StepParams& P, const SimPtrs& Q) {
+  return P.coefG + (size_t)Q.model * P.n_gamma;
+}
 
 // ------------------------------------------------------------------ helpers
 // Asynchronous global -> shared copies (cp.async): a thread issues all its copies
@@ -462,7 +490,7 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_plane_mass(const __grid_consta
   const int nx = P.nx, ny = P.ny, hx = P.hx;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = C::gx(P);
-  const float* c2 = P.c2 + voff;
+  const float* c2 = c2_of(P, S) + voff;
   const float* rx = S.rho[0] + voff;
   const float* rz = S.rho[2] + voff;
   // component order x (spec[2]), z (spec[1]), y (spec[0]); the last one assembles p
@@ -530,29 +558,29 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_plane_mass(const __grid_consta
           S.rho[0][vx] += a;
           S.rho[1][vx] += a;
           S.rho[2][vx] += a;
-          zf[P.us_pf[u]] += P.c2[vx] * (3.f * a);
+          zf[P.us_pf[u]] += c2_of(P, S)[vx] * (3.f * a);
         }
       } else if (role == ROLE_ADJOINT) {
         const float* q = P.qf + ((size_t)shot * P.nt + tix) * P.n_rec;
         for (int u = P.ur_ptr[key0] + lane; u < P.ur_ptr[key0 + nl]; u += 32) {
           float s = 0.f;
           for (int e = P.ur_mptr[u]; e < P.ur_mptr[u + 1]; ++e) s += q[P.ur_mem[e]];
-          const float a = P.ur_coef[u] * s;
+          const float a = ur_coef_of(P, S)[u] * s;
           const int vx = P.ur_vox[u];
           S.rho[0][vx] += a;
           S.rho[1][vx] += a;
           S.rho[2][vx] += a;
-          zf[P.ur_pf[u]] += P.c2[vx] * (3.f * a);
+          zf[P.ur_pf[u]] += c2_of(P, S)[vx] * (3.f * a);
         }
       } else {  // TR: rho_xi(layer) <- g^(Nt - m) / (3 c0^2)
         const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1 - tix)) * P.n_layer;
         for (int j = P.lay_ptr[key0] + lane; j < P.lay_ptr[key0 + nl]; j += 32) {
           const int vx = P.lay_vox[j];
-          const float val = g[j] * P.inv3c2[j];
+          const float val = g[j] * inv3c2_of(P, S)[j];
           S.rho[0][vx] = val;
           S.rho[1][vx] = val;
           S.rho[2][vx] = val;
-          zf[P.lay_pf[j]] = P.c2[vx] * (3.f * val);
+          zf[P.lay_pf[j]] = c2_of(P, S)[vx] * (3.f * val);
         }
       }
       __syncwarp();
@@ -565,7 +593,7 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_plane_mass(const __grid_consta
         }
       } else {
         float* out = role == ROLE_ADJOINT ? P.pa + (size_t)shot * P.n_gamma
-                                          : P.ring + ((size_t)shot * 3 + P.slot[blockIdx.y]) * P.n_gamma;
+                                          : P.ring + ((size_t)shot * kRing + P.slot[blockIdx.y]) * P.n_gamma;
         for (int j = P.gam_ptr[key0] + lane; j < P.gam_ptr[key0 + nl]; j += 32) out[j] = zf[P.gam_pf[j]];
       }
       __syncwarp();
@@ -594,7 +622,7 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_tr_init(const __grid_constant_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = C::gx(P);
   const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1)) * P.n_layer;
-  float* out = P.ring + ((size_t)shot * 3 + 0) * P.n_gamma;
+  float* out = P.ring + ((size_t)shot * kRing + 0) * P.n_gamma;
   __syncthreads();
   for (int p0 = warp * G; p0 < P.npair; p0 += nw * G) {
     const int nl = min(G, P.npair - p0);
@@ -803,7 +831,7 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_xpass_mass(const __grid_consta
   const int p0 = (blockIdx.x * nw + warp) * G;
   if (p0 >= P.npair) return;
   const int nl = min(G, P.npair - p0);
-  const float* c2 = P.c2 + voff;
+  const float* c2 = c2_of(P, S) + voff;
   const float* rx = S.rho[0] + voff;
   const float* rz = S.rho[2] + voff;
   for (int cc = 0; cc < 3; ++cc) {
@@ -869,29 +897,29 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_xpass_mass(const __grid_consta
         S.rho[0][vx] += a;
         S.rho[1][vx] += a;
         S.rho[2][vx] += a;
-        zf[P.us_pf[u]] += P.c2[vx] * (3.f * a);
+        zf[P.us_pf[u]] += c2_of(P, S)[vx] * (3.f * a);
       }
     } else if (role == ROLE_ADJOINT) {
       const float* q = P.qf + ((size_t)shot * P.nt + tix) * P.n_rec;
       for (int u = P.ur_ptr[key0] + lane; u < P.ur_ptr[key0 + nl]; u += 32) {
         float s = 0.f;
         for (int e = P.ur_mptr[u]; e < P.ur_mptr[u + 1]; ++e) s += q[P.ur_mem[e]];
-        const float a = P.ur_coef[u] * s;
+        const float a = ur_coef_of(P, S)[u] * s;
         const int vx = P.ur_vox[u];
         S.rho[0][vx] += a;
         S.rho[1][vx] += a;
         S.rho[2][vx] += a;
-        zf[P.ur_pf[u]] += P.c2[vx] * (3.f * a);
+        zf[P.ur_pf[u]] += c2_of(P, S)[vx] * (3.f * a);
       }
     } else {
       const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1 - tix)) * P.n_layer;
       for (int j = P.lay_ptr[key0] + lane; j < P.lay_ptr[key0 + nl]; j += 32) {
         const int vx = P.lay_vox[j];
-        const float val = g[j] * P.inv3c2[j];
+        const float val = g[j] * inv3c2_of(P, S)[j];
         S.rho[0][vx] = val;
         S.rho[1][vx] = val;
         S.rho[2][vx] = val;
-        zf[P.lay_pf[j]] = P.c2[vx] * (3.f * val);
+        zf[P.lay_pf[j]] = c2_of(P, S)[vx] * (3.f * val);
       }
     }
     __syncwarp();
@@ -904,7 +932,7 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_xpass_mass(const __grid_consta
       }
     } else {
       float* out = role == ROLE_ADJOINT ? P.pa + (size_t)shot * P.n_gamma
-                                        : P.ring + ((size_t)shot * 3 + P.slot[blockIdx.z]) * P.n_gamma;
+                                        : P.ring + ((size_t)shot * kRing + P.slot[blockIdx.z]) * P.n_gamma;
       for (int j = P.gam_ptr[key0] + lane; j < P.gam_ptr[key0 + nl]; j += 32) out[j] = zf[P.gam_pf[j]];
     }
     __syncwarp();
@@ -940,7 +968,7 @@ __global__ void __launch_bounds__(kTpbPlane, 2) k_xpass_tr_init(const __grid_con
   const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1)) * P.n_layer;
   for (int j = P.lay_ptr[key0] + lane; j < P.lay_ptr[key0 + nl]; j += 32) zf[P.lay_pf[j]] = g[j];
   __syncwarp();
-  float* out = P.ring + ((size_t)shot * 3 + 0) * P.n_gamma;
+  float* out = P.ring + ((size_t)shot * kRing + 0) * P.n_gamma;
   for (int j = P.gam_ptr[key0] + lane; j < P.gam_ptr[key0 + nl]; j += 32) out[j] = zf[P.gam_pf[j]];
   __syncwarp();
   C::template fft_x<false>(reg, nl, P, twx, lane);

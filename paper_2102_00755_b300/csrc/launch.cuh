@@ -10,6 +10,15 @@
 
 namespace fwi {
 
+// Raise a kernel's dynamic shared-memory limit to the device's per-block opt-in maximum
+// `cap` less the kernel's static shared memory (static + dynamic may not exceed cap).
+template <class F>
+void set_smem_cap(F* f, int cap) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, f) == cudaSuccess) cap -= (int)a.sharedSizeBytes;
+  cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
+
 // two-step plane kernels for square planes of side N (plane2.cuh):
 // kind 0 = k_plane2_mom, 1 = k_plane2_mass
 template <int N> void launch_plane2(int kind, dim3 grid, size_t smem, cudaStream_t st, const StepParams& P);

@@ -38,9 +38,6 @@ namespace fwi {
 #ifndef P2_REMAP
 #define P2_REMAP 1
 #endif
-#ifndef P2_MERGE
-#define P2_MERGE 1
-#endif
 #ifndef P2_NT128
 #define P2_NT128 640
 #endif
@@ -114,6 +111,22 @@ __device__ __forceinline__ void p2_fetch_rows(float2* Gb, const float* __restric
   }
   cp_async_commit();
 }
+
+// the NY staged rows of G (padded layout of p2_fetch_rows) -> a global field plane, 16-byte
+// stores, consecutive threads on consecutive 16-byte pieces of a row
+template <class G>
+__device__ __forceinline__ void p2_store_rows(const float2* Gb, float* __restrict__ dst) {
+  constexpr int per_row = G::NXc / 4;
+  const float* d = reinterpret_cast<const float*>(Gb);
+  for (int i = threadIdx.x; i < G::NYc * per_row; i += G::NT) {
+    const int y = i / per_row, c = i - y * per_row;
+    *reinterpret_cast<float4*>(dst + y * G::NXc + 4 * c) = *reinterpret_cast<const float4*>(d + G::row_off(y) + 4 * c);
+  }
+}
+
+#ifndef P2_STORE_PASS
+#define P2_STORE_PASS 1
+#endif
 
 #ifndef P2_STAGE_STATE
 #define P2_STAGE_STATE 1
@@ -340,7 +353,9 @@ __device__ __forceinline__ float old_value(const float* p) {
 
 // phase 4, momentum: derivative of both rows in registers, v_comp update in place
 // (Lambda^s (Lambda^s v - dt/rho0 d+ p)), then forward x step A of the new v -> out
-template <class G, bool GIN>
+// SPASS: the new values overwrite the staged old ones (rows in shared memory) instead of
+// going to global memory; p2_store_rows then writes the rows out with 16-byte stores.
+template <class G, bool GIN, bool SPASS = false>
 __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, const float2* twxT,
                                               float* __restrict__ v, const float* vin,
                                               const float* __restrict__ lam, int comp, float lz, float dtr,
@@ -384,11 +399,13 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
       if constexpr (PRE) { o0v = s0[k2]; o1v = s1[k2]; }
       else { o0v = old_value<GIN>(&i0[G::AX1 * k2]); o1v = has1 ? old_value<GIN>(&i1[G::AX1 * k2]) : 0.f; }
       const float n0 = a0 * (a0 * o0v - dtr * z[k2].x);
-      v0p[G::AX1 * k2] = n0;
+      if constexpr (SPASS) const_cast<float*>(i0)[G::AX1 * k2] = n0;
+      else v0p[G::AX1 * k2] = n0;
       float n1 = 0.f;
       if (has1) {
         n1 = a1 * (a1 * o1v - dtr * z[k2].y);
-        v1p[G::AX1 * k2] = n1;
+        if constexpr (SPASS) const_cast<float*>(i1)[G::AX1 * k2] = n1;
+        else v1p[G::AX1 * k2] = n1;
       }
       z[k2] = make_float2(n0, n1);
     });
@@ -397,13 +414,12 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
 }
 
 // phase 4, mass: rho_comp <- Lambda (Lambda rho - dt rho0 d- v); for the last
-// component also p = c0^2 (rho_x + rho_y + rho_z), written as pairs to pout.
-template <class G, bool LAST, bool GIN>
+// component the new rho_y is also written as pairs to pout, where p2_assemble_p turns
+// it into p = c0^2 (rho_x + rho_y + rho_z).
+template <class G, bool LAST, bool GIN, bool SPASS = false>
 __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, float* __restrict__ rho,
                                                const float* rin, const float* __restrict__ lam,
-                                               int comp, float lz, float dtr0, const float* __restrict__ rx,
-                                               const float* __restrict__ rz, const float* __restrict__ c2,
-                                               int nyl) {
+                                               int comp, float lz, float dtr0, int nyl) {
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
     int p, k1;
     p2_task4<G>(t, p, k1);
@@ -441,18 +457,64 @@ __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, fl
       if constexpr (PRE) { o0v = s0[k2]; o1v = s1[k2]; }
       else { o0v = old_value<GIN>(&i0[xo]); o1v = has1 ? old_value<GIN>(&i1[xo]) : 0.f; }
       const float r0 = a0 * (a0 * o0v - dtr0 * z[k2].x);
-      rho[o0 + xo] = r0;
+      if constexpr (SPASS) const_cast<float*>(i0)[xo] = r0;
+      else rho[o0 + xo] = r0;
       float r1 = 0.f;
       if (has1) {
         r1 = a1 * (a1 * o1v - dtr0 * z[k2].y);
-        rho[o1 + xo] = r1;
+        if constexpr (SPASS) const_cast<float*>(i1)[xo] = r1;
+        else rho[o1 + xo] = r1;
       }
-      if (LAST) {
-        const float p0v = __ldg(&c2[o0 + xo]) * (rx[o0 + xo] + r0 + rz[o0 + xo]);
-        const float p1v = has1 ? __ldg(&c2[o1 + xo]) * (rx[o1 + xo] + r1 + rz[o1 + xo]) : 0.f;
-        po[xo] = make_float2(p0v, p1v);
-      }
+      if (LAST) po[xo] = make_float2(r0, r1);
     });
+  }
+}
+
+// p = c0^2 (rho_x + rho_y + rho_z) on the rows held as pairs in X (Alg. 1, pressure-density
+// relation): the new rho_y of pair q is at X[q PST + x] (rows 2q, 2q + 1), rho_x, rho_z and
+// c0^2 come from global rows (row length NX, first row at the pointers).  Consecutive
+// threads take consecutive x, 16 bytes per load where rows allow it, so the three arrays
+// are read in full 128-byte lines with a quarter of the load instructions of a per-voxel
+// gather.  rho_x and rho_z were written earlier in this launch by the same CTA, with a
+// block barrier in between: they are read with ordinary (coherent) loads.  The sum is
+// formed as (rho_x + rho_y) + rho_z.
+template <class G>
+__device__ __forceinline__ void p2_assemble_p(float2* X, const float* rx, const float* rz,
+                                              const float* __restrict__ c2, int nyl) {
+  constexpr int NXc = G::NXc;
+  constexpr int V = NXc % 4 == 0 ? 4 : 1;
+  constexpr int QV = NXc / V;
+  const int npl = (nyl + 1) / 2;
+  for (int t = threadIdx.x; t < npl * QV; t += G::NT) {
+    const int q = t / QV, x = V * (t - q * QV);
+    const int y0 = 2 * q;
+    const bool has1 = y0 + 1 < nyl;
+    const int o0 = y0 * NXc + x, o1 = o0 + NXc;
+    float2* xp = X + q * G::PST + x;
+    if constexpr (V == 4) {
+      const float4 a0 = *reinterpret_cast<const float4*>(rx + o0);
+      const float4 b0 = *reinterpret_cast<const float4*>(rz + o0);
+      const float4 c0 = __ldg(reinterpret_cast<const float4*>(c2 + o0));
+      float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = a1, c1 = a1;
+      if (has1) {
+        a1 = *reinterpret_cast<const float4*>(rx + o1);
+        b1 = *reinterpret_cast<const float4*>(rz + o1);
+        c1 = __ldg(reinterpret_cast<const float4*>(c2 + o1));
+      }
+      const float av0[4] = {a0.x, a0.y, a0.z, a0.w}, bv0[4] = {b0.x, b0.y, b0.z, b0.w};
+      const float cv0[4] = {c0.x, c0.y, c0.z, c0.w}, av1[4] = {a1.x, a1.y, a1.z, a1.w};
+      const float bv1[4] = {b1.x, b1.y, b1.z, b1.w}, cv1[4] = {c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 r = xp[j];
+        xp[j] = make_float2(cv0[j] * (av0[j] + r.x + bv0[j]), has1 ? cv1[j] * (av1[j] + r.y + bv1[j]) : 0.f);
+      }
+    } else {
+      const float2 r = xp[0];
+      const float p0v = __ldg(&c2[o0]) * (rx[o0] + r.x + rz[o0]);
+      const float p1v = has1 ? __ldg(&c2[o1]) * (rx[o1] + r.y + rz[o1]) : 0.f;
+      xp[0] = make_float2(p0v, p1v);
+    }
   }
 }
 
@@ -462,6 +524,39 @@ template <class G>
 __device__ __forceinline__ int p2_pf(int pf) {
   const int q = pf / (4 * G::HX);
   return pf + q * (2 * G::PST - 4 * G::HX);
+}
+
+// Record the pressure on Gamma for the entries [j0, j1) of this CTA's Gamma list: the
+// adjoint role writes pa (first adding the previous iteration's term of the gradient,
+// acc += 2/(dt c0^3) (P(s0) - 2 P(s1) + P(s2)) pa_old, in FP64, when P.acc_prev is set:
+// Alg. 1's accumulation, deferred by one launch because P(s2) is written by the TR
+// simulations of the launch that produced pa_old), the TR role writes its ring slot.
+// `at(pf)` maps a list offset to the shared plane buffer.
+template <class AT>
+__device__ __forceinline__ void p2_record_gamma(const StepParams& P, const SimPtrs& Q, const float* zf, int role,
+                                                int shot, int slot, int j0, int j1, int stride, AT at) {
+  if (role == ROLE_ADJOINT) {
+    float* pa = P.pa + (size_t)shot * P.n_gamma;
+    if (P.acc_prev) {
+      const size_t n = P.n_gamma;
+      const float* rk = P.ring + (size_t)shot * kRing * n;
+      const float* r0 = rk + P.acc_slot[0] * n;
+      const float* r1 = rk + P.acc_slot[1] * n;
+      const float* r2 = rk + P.acc_slot[2] * n;
+      double* acc = P.acc + (size_t)shot * n;
+      const float* cg = coefG_of(P, Q);
+      for (int j = j0 + (int)threadIdx.x; j < j1; j += stride) {
+        const double d2 = (double)r0[j] - 2.0 * (double)r1[j] + (double)r2[j];
+        acc[j] += (double)cg[j] * d2 * (double)pa[j];
+        pa[j] = zf[at(P.gam_pf[j])];
+      }
+    } else {
+      for (int j = j0 + (int)threadIdx.x; j < j1; j += stride) pa[j] = zf[at(P.gam_pf[j])];
+    }
+  } else {
+    float* out = P.ring + ((size_t)shot * kRing + slot) * P.n_gamma;
+    for (int j = j0 + (int)threadIdx.x; j < j1; j += stride) out[j] = zf[at(P.gam_pf[j])];
+  }
 }
 
 template <int NX, int NY>
@@ -488,46 +583,45 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mom(const __gr
   if constexpr (G::STAGE) p2_fetch_spec<G>(Gb, src_of(2));
   p2_stage_twiddles<G>(sm2, P);
   const float lz = __ldg(&P.lams[2][z]);
-  if constexpr (P2_MERGE) {
-    if constexpr (G::STAGE) cp_async_wait_all();
-    __syncthreads();
-    phase1(comp_of(0));
-  }
+  if constexpr (G::STAGE) cp_async_wait_all();
+  __syncthreads();
+  phase1(comp_of(0));
 #pragma unroll 1
   for (int cc = 0; cc < 3; ++cc) {
     const int comp = comp_of(cc);
     float2* dst = (comp == 2 ? Q.spec[1] : (comp == 0 ? Q.spec[2] : Q.spec[0])) + soff;
     float* vg = Q.v[comp] + voff;
-    if constexpr (!P2_MERGE) {
-      if constexpr (G::STAGE) cp_async_wait_all();
-      __syncthreads();
-      phase1(comp);
-    }
+    constexpr bool SS = G::STAGE && P2_STAGE_STATE;
     __syncthreads();
-    if constexpr (G::STAGE && P2_STAGE_STATE) p2_fetch_rows<G>(Gb, vg);      // overlaps phases 2 and 3
+    if constexpr (SS) p2_fetch_rows<G>(Gb, vg);      // overlaps phases 2 and 3
     p2_y_b<G, true>(S, X, nullptr);
     __syncthreads();
     p2_xinv_a<G>(X, S, twx);
+    if constexpr (SS) cp_async_wait_all();
+    __syncthreads();
+    constexpr bool SP = SS && P2_STORE_PASS;
+    p2_mom_update<G, !SS, SP>(S, X, twxT, vg, SS ? reinterpret_cast<const float*>(Gb) : vg, P.lams[comp], comp,
+                              lz, P.dt_over_rho0, NY);
+    __syncthreads();
+    if constexpr (SP) {                              // new v rows out; the next spectrum overlaps 6-7
+      p2_xfwd_b<G>(X, S);
+      p2_store_rows<G>(Gb, vg);
+      __syncthreads();
+      if (cc < 2) p2_fetch_spec<G>(Gb, src_of(comp_of(cc + 1)));
+    } else {
+      if constexpr (G::STAGE) {                      // next spectrum overlaps phases 5-7
+        if (cc < 2) p2_fetch_spec<G>(Gb, src_of(comp_of(cc + 1)));
+      }
+      p2_xfwd_b<G>(X, S);
+      __syncthreads();
+    }
+    p2_yfwd_a<G>(S, X, twy);
     if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
-    constexpr bool SS = G::STAGE && P2_STAGE_STATE;
-    p2_mom_update<G, !SS>(S, X, twxT, vg, SS ? reinterpret_cast<const float*>(Gb) : vg, P.lams[comp], comp, lz,
-                          P.dt_over_rho0, NY);
-    __syncthreads();
-    if constexpr (G::STAGE) {                               // next spectrum overlaps phases 5-7
-      if (cc < 2) p2_fetch_spec<G>(Gb, src_of(comp_of(cc + 1)));
-    }
-    p2_xfwd_b<G>(X, S);
-    __syncthreads();
-    p2_yfwd_a<G>(S, X, twy);
-    if constexpr (P2_MERGE && G::STAGE) cp_async_wait_all();
-    __syncthreads();
     p2_y_b<G, false>(X, nullptr, dst);
-    // with P2_MERGE, phase 1 of the next component shares this interval: it writes S
-    // (last read by phase 6) from the staged spectrum, phase 7 reads X
-    if constexpr (P2_MERGE) {
-      if (cc < 2) phase1(comp_of(cc + 1));
-    }
+    // phase 1 of the next component shares this interval: it writes S (last read by
+    // phase 6) from the staged spectrum, phase 7 reads X
+    if (cc < 2) phase1(comp_of(cc + 1));
   }
 }
 
@@ -553,6 +647,9 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
   // the end of phase 3 to the next phase 2; rho rows in the staging buffer.
   if constexpr (G::STAGE) p2_fetch_spec<G>(Gb, Q.spec[2] + soff);
   p2_stage_twiddles<G>(sm2, P);
+  constexpr bool SS = G::STAGE && P2_STAGE_STATE;
+  constexpr bool SP = SS && P2_STORE_PASS;           // new rho rows leave through the staged rows
+  float* rprev = nullptr;                            // component whose new rows wait in Gb
 #pragma unroll 1
   for (int cc = 0; cc < 3; ++cc) {
     const int comp = cc == 0 ? 0 : (cc == 1 ? 2 : 1);
@@ -561,24 +658,28 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
     cp_async_wait_all();
     __syncthreads();
     p2_yinv_a<G>(S, src, comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.am[comp], twy);
+    if constexpr (SP) {
+      if (cc > 0) p2_store_rows<G>(Gb, rprev);
+    }
     __syncthreads();
-    if constexpr (G::STAGE && P2_STAGE_STATE) p2_fetch_rows<G>(Gb, rg);      // overlaps phases 2 and 3
+    if constexpr (SS) p2_fetch_rows<G>(Gb, rg);      // overlaps phases 2 and 3
     p2_y_b<G, true>(S, X, nullptr);
     __syncthreads();
     p2_xinv_a<G>(X, S, twx);
-    if constexpr (G::STAGE) cp_async_wait_all();
+    if constexpr (SS) cp_async_wait_all();
     __syncthreads();
-    constexpr bool SS = G::STAGE && P2_STAGE_STATE;
     const float* rin = SS ? reinterpret_cast<const float*>(Gb) : rg;
     if (cc < 2) {
       p2_fetch_spec<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff);   // overlaps phase 4
-      p2_mass_update<G, false, !SS>(S, nullptr, rg, rin, P.lam[comp], comp, lz, P.dt_rho0, nullptr, nullptr,
-                                    nullptr, NY);
+      p2_mass_update<G, false, !SS, SP>(S, nullptr, rg, rin, P.lam[comp], comp, lz, P.dt_rho0, NY);
     } else {
-      p2_mass_update<G, true, !SS>(S, X, rg, rin, P.lam[1], 1, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
-                                   P.c2 + voff, NY);
+      p2_mass_update<G, true, !SS, SP>(S, X, rg, rin, P.lam[1], 1, lz, P.dt_rho0, NY);
     }
+    rprev = rg;
   }
+  __syncthreads();
+  if constexpr (SP) p2_store_rows<G>(Gb, rprev);
+  p2_assemble_p<G>(X, Q.rho[0] + voff, Q.rho[2] + voff, c2_of(P, Q) + voff, NY);
   __syncthreads();
   // sparse updates of rho_xi and p on this plane, then recording
   const int key0 = z * G::NP, key1 = key0 + G::NP;
@@ -591,29 +692,29 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
       Q.rho[0][vx] += a;
       Q.rho[1][vx] += a;
       Q.rho[2][vx] += a;
-      zf[p2_pf<G>(P.us_pf[u])] += P.c2[vx] * (3.f * a);
+      zf[p2_pf<G>(P.us_pf[u])] += c2_of(P, Q)[vx] * (3.f * a);
     }
   } else if (role == ROLE_ADJOINT) {
     const float* q = P.qf + ((size_t)shot * P.nt + tix) * P.n_rec;
     for (int u = P.ur_ptr[key0] + threadIdx.x; u < P.ur_ptr[key1]; u += G::NT) {
       float s = 0.f;
       for (int e = P.ur_mptr[u]; e < P.ur_mptr[u + 1]; ++e) s += q[P.ur_mem[e]];
-      const float a = P.ur_coef[u] * s;
+      const float a = ur_coef_of(P, Q)[u] * s;
       const int vx = P.ur_vox[u];
       Q.rho[0][vx] += a;
       Q.rho[1][vx] += a;
       Q.rho[2][vx] += a;
-      zf[p2_pf<G>(P.ur_pf[u])] += P.c2[vx] * (3.f * a);
+      zf[p2_pf<G>(P.ur_pf[u])] += c2_of(P, Q)[vx] * (3.f * a);
     }
   } else {  // TR: rho_xi(layer) <- g^(Nt - m) / (3 c0^2)
     const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1 - tix)) * P.n_layer;
     for (int j = P.lay_ptr[key0] + threadIdx.x; j < P.lay_ptr[key1]; j += G::NT) {
       const int vx = P.lay_vox[j];
-      const float val = g[j] * P.inv3c2[j];
+      const float val = g[j] * inv3c2_of(P, Q)[j];
       Q.rho[0][vx] = val;
       Q.rho[1][vx] = val;
       Q.rho[2][vx] = val;
-      zf[p2_pf<G>(P.lay_pf[j])] = P.c2[vx] * (3.f * val);
+      zf[p2_pf<G>(P.lay_pf[j])] = c2_of(P, Q)[vx] * (3.f * val);
     }
   }
   __syncthreads();
@@ -625,9 +726,8 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
       for (int j = P.lay_ptr[key0] + threadIdx.x; j < P.lay_ptr[key1]; j += G::NT) g[j] = zf[p2_pf<G>(P.lay_pf[j])];
     }
   } else {
-    float* out = role == ROLE_ADJOINT ? P.pa + (size_t)shot * P.n_gamma
-                                      : P.ring + ((size_t)shot * 3 + P.slot[blockIdx.y]) * P.n_gamma;
-    for (int j = P.gam_ptr[key0] + threadIdx.x; j < P.gam_ptr[key1]; j += G::NT) out[j] = zf[p2_pf<G>(P.gam_pf[j])];
+    p2_record_gamma(P, Q, zf, role, shot, P.slot[blockIdx.y], P.gam_ptr[key0], P.gam_ptr[key1], G::NT,
+                    [](int pf) { return p2_pf<G>(pf); });
   }
   __syncthreads();
   // forward x step A of p (pairs in X) -> S, then step B, R2C unpacking and y

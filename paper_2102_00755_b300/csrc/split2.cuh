@@ -392,13 +392,13 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mass(const __grid
     const float* rin = G::STG ? R : rg;
     if (cc < 2) {
       x2_load_rows<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff, p0, ny);   // overlaps the update
-      p2_mass_update<G, false, !G::STG>(S, nullptr, rg, rin, lam, comp, lz, P.dt_rho0, nullptr, nullptr, nullptr,
-                                        nyl);
+      p2_mass_update<G, false, !G::STG>(S, nullptr, rg, rin, lam, comp, lz, P.dt_rho0, nyl);
     } else {
-      p2_mass_update<G, true, !G::STG>(S, X, rg, rin, lam, comp, lz, P.dt_rho0, Q.rho[0] + voff, Q.rho[2] + voff,
-                                       P.c2 + voff, nyl);
+      p2_mass_update<G, true, !G::STG>(S, X, rg, rin, lam, comp, lz, P.dt_rho0, nyl);
     }
   }
+  __syncthreads();
+  p2_assemble_p<G>(X, Q.rho[0] + voff, Q.rho[2] + voff, c2_of(P, Q) + voff, nyl);
   __syncthreads();
   // sparse updates of rho_xi and p on these pairs, then recording.  List offsets pf
   // address pair regions of 2 hx complex of the whole plane; here pair p0 + q sits at
@@ -417,29 +417,29 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mass(const __grid
       Q.rho[0][vx] += a;
       Q.rho[1][vx] += a;
       Q.rho[2][vx] += a;
-      zf[loc(P.us_pf[u])] += P.c2[vx] * (3.f * a);
+      zf[loc(P.us_pf[u])] += c2_of(P, Q)[vx] * (3.f * a);
     }
   } else if (role == ROLE_ADJOINT) {
     const float* q = P.qf + ((size_t)shot * P.nt + tix) * P.n_rec;
     for (int u = P.ur_ptr[key0] + threadIdx.x; u < P.ur_ptr[key1]; u += G::NT) {
       float s = 0.f;
       for (int e = P.ur_mptr[u]; e < P.ur_mptr[u + 1]; ++e) s += q[P.ur_mem[e]];
-      const float a = P.ur_coef[u] * s;
+      const float a = ur_coef_of(P, Q)[u] * s;
       const int vx = P.ur_vox[u];
       Q.rho[0][vx] += a;
       Q.rho[1][vx] += a;
       Q.rho[2][vx] += a;
-      zf[loc(P.ur_pf[u])] += P.c2[vx] * (3.f * a);
+      zf[loc(P.ur_pf[u])] += c2_of(P, Q)[vx] * (3.f * a);
     }
   } else {  // TR: rho_xi(layer) <- g^(Nt - m) / (3 c0^2)
     const float* g = P.ghist + ((size_t)shot * P.nt + (P.nt - 1 - tix)) * P.n_layer;
     for (int j = P.lay_ptr[key0] + threadIdx.x; j < P.lay_ptr[key1]; j += G::NT) {
       const int vx = P.lay_vox[j];
-      const float val = g[j] * P.inv3c2[j];
+      const float val = g[j] * inv3c2_of(P, Q)[j];
       Q.rho[0][vx] = val;
       Q.rho[1][vx] = val;
       Q.rho[2][vx] = val;
-      zf[loc(P.lay_pf[j])] = P.c2[vx] * (3.f * val);
+      zf[loc(P.lay_pf[j])] = c2_of(P, Q)[vx] * (3.f * val);
     }
   }
   __syncthreads();
@@ -451,9 +451,7 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mass(const __grid
       for (int j = P.lay_ptr[key0] + threadIdx.x; j < P.lay_ptr[key1]; j += G::NT) g[j] = zf[loc(P.lay_pf[j])];
     }
   } else {
-    float* out = role == ROLE_ADJOINT ? P.pa + (size_t)shot * P.n_gamma
-                                      : P.ring + ((size_t)shot * 3 + P.slot[blockIdx.z]) * P.n_gamma;
-    for (int j = P.gam_ptr[key0] + threadIdx.x; j < P.gam_ptr[key1]; j += G::NT) out[j] = zf[loc(P.gam_pf[j])];
+    p2_record_gamma(P, Q, zf, role, shot, P.slot[blockIdx.z], P.gam_ptr[key0], P.gam_ptr[key1], G::NT, loc);
   }
   __syncthreads();
   // forward x step A of p (pairs in X) -> S, then step B, R2C unpacking -> rows of spec[0]

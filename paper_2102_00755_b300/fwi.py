@@ -28,7 +28,7 @@ FWI_ENOTSUP = 7
 
 PAIRING = {"literal": 0, "exact": 1}
 
-C_SYMBOLS = ("fwi_plan_create", "fwi_plan_bind_workspace", "fwi_forward", "fwi_gradient",
+C_SYMBOLS = ("fwi_plan_create", "fwi_plan_set_tr_box", "fwi_plan_bind_workspace", "fwi_forward", "fwi_gradient",
              "fwi_forward_delayed", "fwi_gradient_delayed",
              "fwi_plan_status", "fwi_plan_voxel_steps", "fwi_plan_launches", "fwi_plan_profile",
              "fwi_plan_profile_read", "fwi_plan_set_schedule", "fwi_plan_get_schedule",
@@ -70,7 +70,7 @@ class fwi_problem(ctypes.Structure):
         ("layer_idx", ctypes.POINTER(ctypes.c_int32)), ("gamma_idx", ctypes.POINTER(ctypes.c_int32)),
         ("wavelet", ctypes.POINTER(ctypes.c_float)),
         ("pairing", ctypes.c_int32), ("max_shots", ctypes.c_int32),
-        ("sims_per_launch", ctypes.c_int32),
+        ("sims_per_launch", ctypes.c_int32), ("per_shot_models", ctypes.c_int32),
     ]
 
 
@@ -88,6 +88,9 @@ def lib():
         L.fwi_plan_create.argtypes = [ctypes.POINTER(fwi_problem), ctypes.POINTER(sz), ctypes.POINTER(vp)]
         L.fwi_plan_create.restype = ctypes.c_int
         L.fwi_plan_bind_workspace.argtypes = [vp, vp, sz]
+        L.fwi_plan_set_tr_box.restype = ctypes.c_int
+        L.fwi_plan_set_tr_box.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                          ctypes.POINTER(sz)]
         L.fwi_plan_bind_workspace.restype = ctypes.c_int
         L.fwi_forward.argtypes = [vp, vp, vp, i32, vp, vp]
         L.fwi_forward.restype = ctypes.c_int
@@ -175,6 +178,16 @@ def fwi_plan_create(prob: fwi_problem):
     plan = ctypes.c_void_p(0)
     st = lib().fwi_plan_create(ctypes.byref(prob), ctypes.byref(ws), ctypes.byref(plan))
     return st, plan, ws.value
+
+
+def fwi_plan_set_tr_box(plan, origin, size, pml):
+    """(status, new workspace bytes): TR re-simulation on the box [origin, origin + size)
+    with a PML of pml cells inside it (x, y, z each)."""
+    arr = ctypes.c_int32 * 3
+    ws = ctypes.c_size_t(0)
+    st = lib().fwi_plan_set_tr_box(plan, arr(*map(int, origin)), arr(*map(int, size)), arr(*map(int, pml)),
+                                   ctypes.byref(ws))
+    return st, ws.value
 
 
 def fwi_plan_bind_workspace(plan, ptr: int, nbytes: int) -> int:
@@ -364,7 +377,7 @@ class Plan:
 
     def __init__(self, *, nx, ny, nz, pml, dx, dt, c_ref, rho0, pml_alpha, nt, src_idx, rec_idx,
                  layer_idx, gamma_idx, wavelet, pairing="literal", max_shots=1, c_rec=0.0,
-                 sims_per_launch=0, device="cuda", workspace=None):
+                 sims_per_launch=0, device="cuda", workspace=None, tr_box=None, per_shot_models=False):
         import numpy as np
         self._keep = [_i32(src_idx), _i32(rec_idx), _i32(layer_idx), _i32(gamma_idx),
                       np.ascontiguousarray(wavelet, dtype=np.float32)]
@@ -383,10 +396,16 @@ class Plan:
         P.pairing = PAIRING[pairing] if isinstance(pairing, str) else int(pairing)
         P.max_shots = max_shots
         P.sims_per_launch = sims_per_launch
+        P.per_shot_models = 1 if per_shot_models else 0
+        self.per_shot_models = bool(per_shot_models)
         self.prob = P
         st, plan, nbytes = fwi_plan_create(P)
         _check(st, "fwi_plan_create")
         self.handle = plan
+        self.tr_box = tr_box
+        if tr_box is not None:            # (origin, size, pml): TR re-simulation on a box (Sec. 3.1)
+            st, nbytes = fwi_plan_set_tr_box(plan, *tr_box)
+            _check(st, "fwi_plan_set_tr_box")
         self.workspace_bytes = nbytes
         self.nx, self.ny, self.nz, self.nt = nx, ny, nz, nt
         self.n_src, self.n_rec, self.max_shots = len(s), len(r), max_shots
@@ -421,6 +440,7 @@ class Plan:
         K = weights.shape[0]
         if traces is None:
             traces = torch.empty((K, self.nt, self.n_rec), dtype=torch.float32, device=c.device)
+        self._check_sizes(K, c, weights, traces=traces, delays=delays)
         if delays is None:
             st = fwi_forward(self.handle, _dptr(c, torch.float32, "c"), _dptr(weights, torch.float32, "weights"),
                              K, _dptr(traces, torch.float32, "traces"), _stream_handle(stream))
@@ -440,7 +460,11 @@ class Plan:
         if misfit is None:
             misfit = torch.empty(K, dtype=torch.float64, device=c.device)
         if grad is None:
-            grad = torch.empty(self.n_vox, dtype=torch.float64, device=c.device)
+            grad = torch.empty((K if self.per_shot_models else 1) * self.n_vox, dtype=torch.float64,
+                               device=c.device)
+        obs_nt = observed.shape[1] if (delays is not None and observed.dim() == 3) else self.nt
+        self._check_sizes(K, c, weights, traces=traces, delays=delays, grad=grad, misfit=misfit,
+                          observed=observed, encoded=encoded, obs_nt=obs_nt)
         tp = _dptr(traces, torch.float32, "traces") if traces is not None else ctypes.c_void_p(0)
         if delays is None:
             st = fwi_gradient(self.handle, _dptr(c, torch.float32, "c"),
@@ -450,7 +474,6 @@ class Plan:
                               tp, _stream_handle(stream))
             _check(st, "fwi_gradient")
         else:
-            obs_nt = observed.shape[1] if observed.dim() == 3 else self.nt
             st = fwi_gradient_delayed(self.handle, _dptr(c, torch.float32, "c"),
                                       _dptr(weights, torch.float32, "weights"),
                                       _dptr(delays, torch.int32, "delays"), K,
@@ -459,6 +482,20 @@ class Plan:
                                       tp, _stream_handle(stream))
             _check(st, "fwi_gradient_delayed")
         return misfit, grad
+
+    def _check_sizes(self, K, c, weights, traces=None, delays=None, grad=None, misfit=None, observed=None,
+                     encoded=True, obs_nt=None):
+        """The C ABI takes bare pointers: refuse tensors smaller than the call will touch."""
+        need = {"c": (c, (K if self.per_shot_models else 1) * self.n_vox),
+                "weights": (weights, K * self.n_src),
+                "traces": (traces, K * self.nt * self.n_rec),
+                "delays": (delays, K * self.n_src),
+                "grad": (grad, (K if self.per_shot_models else 1) * self.n_vox),
+                "misfit": (misfit, K),
+                "observed": (observed, (K if encoded else self.n_src) * (obs_nt or self.nt) * self.n_rec)}
+        for name, (t, n) in need.items():
+            if t is not None and t.numel() < n:
+                raise ValueError(f"{name}: {t.numel()} elements, the call needs {n}")
 
     def status(self) -> int:
         return fwi_plan_status(self.handle)
@@ -504,14 +541,27 @@ class Batch:
         self.plans = list(plans)
         st, self.handle = fwi_batch_create([p.handle for p in self.plans])
         _check(st, "fwi_batch_create")
+        self._out = None     # output buffers kept across calls (they are part of the graph key)
 
     def gradient(self, cs, weights, observed, encoded=None, misfits=None, grads=None, stream=None):
+        """Gradients of every member plan in one graph launch.  Without misfits/grads the
+        batch returns its own output buffers, the same tensors on every call with the same
+        shot counts, so that repeated calls replay the captured graph instead of capturing
+        a new one (new output pointers would change the graph key); copy them before the
+        next call if they must be kept."""
         n = len(self.plans)
         encoded = encoded or [True] * n
-        if misfits is None:
-            misfits = [torch.empty(w.shape[0], dtype=torch.float64, device=c.device) for c, w in zip(cs, weights)]
-        if grads is None:
-            grads = [torch.empty(p.n_vox, dtype=torch.float64, device=c.device) for p, c in zip(self.plans, cs)]
+        if misfits is None or grads is None:
+            shape = tuple((w.shape[0], str(c.device)) for c, w in zip(cs, weights))
+            if self._out is None or self._out[0] != shape:
+                self._out = (shape,
+                             [torch.empty(w.shape[0], dtype=torch.float64, device=c.device)
+                              for c, w in zip(cs, weights)],
+                             [torch.empty((w.shape[0] if p.per_shot_models else 1) * p.n_vox,
+                                          dtype=torch.float64, device=c.device)
+                              for p, c, w in zip(self.plans, cs, weights)])
+            misfits = self._out[1] if misfits is None else misfits
+            grads = self._out[2] if grads is None else grads
         st = fwi_batch_gradient(self.handle,
                                 [_dptr(c, torch.float32, "c").value for c in cs],
                                 [_dptr(w, torch.float32, "weights").value for w in weights],

@@ -125,7 +125,9 @@ class Server:
         self.use_graphs = use_graphs
         self.pool: Dict[str, List[_Slot]] = {name: [] for name in self.levels}
         self.reserved = 0
-        self.refused_for_memory = 0
+        self.refused_for_memory = 0      # requests that had to wait for memory (each counted once)
+        self._refused = set()
+        self._need = {}                  # slot bytes per level (a plan is built once to size it)
 
     def _slot_bytes(self, level: Level) -> int:
         wl = level.wl
@@ -135,14 +137,18 @@ class Server:
         fwi.fwi_plan_destroy(plan)
         return ws + wl.nt * len(wl.rec_idx) * 4 + wl.n_vox * 8
 
-    def _acquire(self, level_name) -> Optional[_Slot]:
+    def _acquire(self, level_name, rid=None) -> Optional[_Slot]:
         for s in self.pool[level_name]:
             if not s.busy:
                 return s
         lv = self.levels[level_name]
-        need = self._slot_bytes(lv)
+        if level_name not in self._need:
+            self._need[level_name] = self._slot_bytes(lv)
+        need = self._need[level_name]
         if self.reserved + need > self.mem_budget:
-            self.refused_for_memory += 1
+            if rid not in self._refused:
+                self._refused.add(rid)
+                self.refused_for_memory += 1
             return None
         s = _Slot(lv, self.device, self.pairing, self.use_graphs)
         self.pool[level_name].append(s)
@@ -197,10 +203,10 @@ class Server:
                 req = pending[i]
                 if realtime and req.arrival > now:
                     break
-                slot = self._acquire(req.level)
+                slot = self._acquire(req.level, req.rid)
                 if slot is None and not inflight:
                     self._release_idle(req.level)
-                    slot = self._acquire(req.level)
+                    slot = self._acquire(req.level, req.rid)
                 if slot is None:
                     break
                 slot.busy = True
@@ -279,18 +285,45 @@ def make_level(name, wl, device="cuda") -> Level:
     return Level(name, wl, c, raw)
 
 
+def stratified_draw(mix: List[float], n: int, rng) -> np.ndarray:
+    """Category of each of n draws with counts exactly proportional to mix (largest-remainder
+    rounding), in a seeded random order."""
+    p = np.asarray(mix, dtype=np.float64) / np.sum(mix)
+    counts = np.floor(p * n).astype(int)
+    rest = p * n - counts
+    for i in np.argsort(-rest, kind="stable")[:n - counts.sum()]:
+        counts[i] += 1
+    cats = np.repeat(np.arange(len(mix)), counts)
+    rng.shuffle(cats)
+    return cats
+
+
 def poisson_stream(levels: List[str], mix: List[float], n: int, rate: float, n_src: int, seed: int,
-                   min_src: int = 2, max_src: int = 8, p_gradient: float = 0.5) -> List[Request]:
+                   min_src: int = 2, max_src: int = 8, p_gradient: float = 0.5,
+                   stratified: bool = False) -> List[Request]:
     """Seeded Poisson arrivals; level by mix weights; kind by p_gradient; 2..8 active
-    emitters with Rademacher weights (the remaining emitters get weight 0)."""
+    emitters with Rademacher weights (the remaining emitters get weight 0).  With
+    stratified=True the level counts are exactly proportional to the mix and each level's
+    requests are split between gradients and forwards by p_gradient (seeded order), so a
+    finite stream carries the intended mix instead of a random draw of it."""
     rng = np.random.default_rng(seed)
     t = 0.0
     p = np.asarray(mix, dtype=np.float64) / np.sum(mix)
     out = []
+    if stratified:
+        lv_of = stratified_draw(mix, n, rng)
+        kind_of = np.zeros(n, dtype=bool)
+        for li in range(len(levels)):
+            idx = np.flatnonzero(lv_of == li)
+            kind_of[idx] = stratified_draw([p_gradient, 1.0 - p_gradient], len(idx), rng) == 0
     for rid in range(n):
         t += rng.exponential(1.0 / rate)
-        lv = levels[rng.choice(len(levels), p=p)]
-        kind = "gradient" if rng.random() < p_gradient else "forward"
+        if stratified:
+            lv = levels[lv_of[rid]]
+            kind = "gradient" if kind_of[rid] else "forward"
+        else:
+            lv = levels[rng.choice(len(levels), p=p)]
+            kind = "gradient" if rng.random() < p_gradient else "forward"
         k = int(rng.integers(min_src, min(max_src, n_src) + 1))
         w = np.zeros(n_src)
         active = rng.choice(n_src, size=k, replace=False)
