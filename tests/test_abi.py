@@ -108,3 +108,30 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(fwi, "LIB_PATH", "/nonexistent/libfwi.so")
     with pytest.raises(ImportError):
         fwi.lib()
+
+
+def test_tr_box_validation_and_workspace(L):
+    """fwi_plan_set_tr_box (Sec. 3.1's TR on a box enclosing Gamma) checks the box on the
+    host and reports the new workspace size: the whole-grid TR states go, the box plan's
+    workspace and the cropped c0 come in.  No device memory is touched."""
+    wl = synth.small_workload(36, 36, 30, 40, pml=4, n_src=3, n_rec=30, K=2, layer=3, seed=5, gamma_frac=0.25)
+    P, keep = _problem(wl)
+    st, plan, nbytes = fwi.fwi_plan_create(P)
+    assert st == fwi.FWI_OK
+    origin, size, pml = synth.tr_box(wl, 2, 3)
+    st, nb_box = fwi.fwi_plan_set_tr_box(plan, origin, size, pml)
+    assert st == fwi.FWI_OK
+    state = 2 * 6 * wl.n_vox * 4                    # K = 2 whole-grid TR states of six fields
+    assert nb_box < nbytes - state // 2
+    assert fwi.fwi_plan_voxel_steps(plan, 2, 1) == 2 * ((2 * wl.nt - 2) * wl.n_vox +
+                                                      (wl.nt - 1) * size[0] * size[1] * size[2])
+    # calling again replaces the box; the grid itself is a valid box
+    st, nb_full = fwi.fwi_plan_set_tr_box(plan, (0, 0, 0), (wl.nx, wl.ny, wl.nz), wl.pml)
+    assert st == fwi.FWI_OK and nb_full > nb_box
+    bad = [((30, 0, 0), size, pml),                 # box leaves the grid
+           (origin, size, (9, 9, 9)),               # Gamma inside the box's PML
+           ((0, 0, 0), (12, 12, 12), pml),          # Gamma outside the box
+           (origin, size, (-1, 3, 3))]
+    for o, s, p in bad:
+        assert fwi.fwi_plan_set_tr_box(plan, o, s, p)[0] == fwi.FWI_EINVAL, (o, s, p)
+    fwi.fwi_plan_destroy(plan)

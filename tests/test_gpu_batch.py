@@ -78,3 +78,42 @@ def test_batch_instance_matches_oracle():
     assert np.all(np.abs(Ds[1].cpu().numpy() - D_ref) <= 1e-3 * np.abs(D_ref))
     g = gs[1].cpu().numpy().reshape(wl_small.shape)
     assert oc.rel(g, g_ref) < 1e-3
+
+
+def test_batch_recaptures_after_rebinding_and_schedule_change():
+    """A member plan bound to a new workspace, or given a new schedule, between two batch
+    calls: the batch must not replay a graph holding the old workspace or launch shapes.
+    The old workspace (still allocated) is zeroed after the rebinding: a stale replay would
+    read empty tables and give other results (zeros keep every table index in bounds)."""
+    from paper_2102_00755_b300 import autotune
+    fbuild.build()
+    wls = _instances(32)[:2]
+    plans, cs, ws, obs = _prepare(wls)
+    alone = [p.gradient(c, w, o) for p, c, w, o in zip(plans, cs, ws, obs)]
+    alone = [(D.clone(), g.clone()) for D, g in alone]
+    batch = fwi.Batch(plans)
+    Ds, gs = batch.gradient(cs, ws, obs)
+    torch.cuda.synchronize()
+    # rebind plan 0 to a fresh workspace; clear the old one (still allocated)
+    p0 = plans[0]
+    old = p0.workspace
+    new = torch.empty_like(old)
+    base = new.data_ptr()
+    aligned = (base + 255) & ~255
+    assert fwi.fwi_plan_bind_workspace(p0.handle, aligned, p0.workspace_bytes) == fwi.FWI_OK
+    p0.workspace = new
+    old.zero_()
+    Ds, gs = batch.gradient(cs, ws, obs)
+    torch.cuda.synchronize()
+    for (D0, g0), D1, g1 in zip(alone, Ds, gs):
+        assert torch.equal(D0, D1) and torch.equal(g0, g1)
+    # a schedule change of plan 1 (z tile 16): the batch follows it like a separate call
+    sched = dict(autotune.get_schedule(plans[1]), z_tile=16)
+    assert autotune.set_schedule(plans[1], sched) == fwi.FWI_OK
+    D1a, g1a = plans[1].gradient(cs[1], ws[1], obs[1])
+    D1a, g1a = D1a.clone(), g1a.clone()
+    Ds, gs = batch.gradient(cs, ws, obs)
+    torch.cuda.synchronize()
+    assert torch.equal(Ds[1], D1a) and torch.equal(gs[1], g1a)
+    assert all(p.status() == fwi.FWI_OK for p in plans)
+    del old

@@ -92,7 +92,8 @@ def test_memory_budget_limits_slots_and_releases_idle_levels(fake):
     assert st["requests"] == 5
     # three small slots fit (90 of 100); the big request waits for memory, is refused while
     # small ones run, then gets memory once the idle small slots are released
-    assert st["refused_for_memory"] >= 1
+    # one request (the big one) had to wait; it is counted once however long it polled
+    assert st["refused_for_memory"] == 1
     assert fake.closed >= 1
     assert srv.reserved <= 100
     order = [e[1] for e in fake.log]
