@@ -169,6 +169,56 @@ def cpu_baseline(wl, budget_s=15.0, min_steps=6):
                       f"grid ({dt:.1f} s); a gradient is 3 simulations of such steps"}
 
 
+def run_oracle_full(args):
+    """Whole FP64 oracle gradients of the 32^3 (300 steps, one source) and 96x96x48 (1000
+    steps, exact pairing) configurations on the host cores, wall clock, median of
+    --oracle-runs, beside the same gradients on the GPU (CUDA events, median of 10)."""
+    import torch
+
+    from oracle import pstd
+    from paper_2102_00755_b300 import fwi, synth
+
+    workers = os.cpu_count() or 1
+    os.environ["ORACLE_WORKERS"] = str(workers)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for name, wl, pairing in [("32^3, 300 steps, 1 source, 64 receivers (literal)", synth.config1(), "literal"),
+                              ("96x96x48, 1000 steps, 32 + 128 transducers (exact)", synth.config4(), "exact")]:
+        G = pstd.grid_for(wl)
+        w = wl.weights[0]
+        f_obs = pstd.forward(G, wl.c_true, wl.src_idx, w, wl.wavelet, wl.rec_idx)[0]
+        ts = []
+        for _ in range(args.oracle_runs):
+            t0 = time.perf_counter()
+            pstd.fwi_gradient(G, wl.c_model, wl.src_idx, w, wl.wavelet, wl.rec_idx, wl.layer_idx,
+                              wl.gamma_idx, f_obs, pairing=pairing, c_rec=wl.c_rec)
+            ts.append(time.perf_counter() - t0)
+        plan = fwi.Plan.from_workload(wl, pairing=pairing, max_shots=1, device=dev)
+        c = torch.tensor(wl.c_model, dtype=torch.float32, device=dev).reshape(-1)
+        wt = torch.tensor(wl.weights, dtype=torch.float32, device=dev)
+        ot = torch.tensor(synth.f32(f_obs)[None], dtype=torch.float32, device=dev)
+        plan.gradient(c, wt, ot)
+        torch.cuda.synchronize(dev)
+        gt = []
+        for _ in range(10):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.gradient(c, wt, ot)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            gt.append(a.elapsed_time(b))
+        assert plan.status() == fwi.FWI_OK
+        vs = plan.voxel_steps(1, True)
+        o_s, g_ms = statistics.median(ts), statistics.median(gt)
+        rows.append({"config": name, "voxel_steps": vs, "oracle_wall_s": ts, "oracle_median_s": o_s,
+                     "oracle_gvoxel_steps_per_s": vs / o_s / 1e9, "gpu_median_ms": g_ms,
+                     "gpu_gvoxel_steps_per_s": vs / (g_ms / 1e3) / 1e9, "gpu_over_oracle": o_s / (g_ms / 1e3)})
+        plan.close()
+    print(json.dumps({"workload": "oracle timing: whole gradients, FP64 oracle vs the GPU path",
+                      "cores": workers, "runs": args.oracle_runs, "rows": rows}), flush=True)
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on bounded samples of the same workload."""
     from paper_2102_00755_b300 import synth
@@ -207,11 +257,14 @@ def run_reference(args):
 
 def run_batch(args):
     """16 encoded-gradient instances of uneven grids (4 each of 64^3, 96x96x48, 128x128x64,
-    160x160x80; 1200..2000 steps) as one captured CUDA graph, against the same instances run
-    one after another (default batching inside each instance, and the plain form)."""
+    160x160x80; 1200..2000 steps).  The batched form groups the instances by grid: one plan
+    per grid whose super-shots are the instances (each with its own model, data and
+    gradient, sharing every launch), the four plans captured as one CUDA graph.  Compared
+    with: one single-instance plan per instance in one graph, the instances one after
+    another, and the plain form (one simulation per launch sequence)."""
     import torch
 
-    from paper_2102_00755_b300 import fwi, synth
+    from paper_2102_00755_b300 import autotune, fwi, synth
 
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
@@ -220,26 +273,30 @@ def run_batch(args):
         for wl in wls:
             wl.nt = args.nt
             wl.wavelet = wl.wavelet[:args.nt]
-    from paper_2102_00755_b300 import autotune
-    tuned = {}
-    for wl in wls:                      # one schedule per grid size, chosen by the autotuner
-        if (wl.nx, wl.ny, wl.nz) not in tuned:
-            tuned[(wl.nx, wl.ny, wl.nz)] = autotune.tune(wl, K=1, steps=24, reps=3, save=False)["schedule"]
-    plans, plains, cs, ws, obs = [], [], [], [], []
+    groups = {}
     for wl in wls:
-        plan = fwi.Plan.from_workload(wl, max_shots=1, device=dev)
-        autotune.set_schedule(plan, tuned[(wl.nx, wl.ny, wl.nz)])
-        w = torch.tensor(wl.weights, dtype=torch.float32, device=dev)
-        obs.append(plan.forward(torch.tensor(wl.c_true, dtype=torch.float32, device=dev).reshape(-1), w))
-        plans.append(plan)
-        cs.append(torch.tensor(wl.c_model, dtype=torch.float32, device=dev).reshape(-1))
-        ws.append(w)
-    vsteps = sum(p.voxel_steps(1, True) for p in plans)
-    Ds = [torch.empty(1, dtype=torch.float64, device=dev) for _ in plans]
-    gs = [torch.empty(p.n_vox, dtype=torch.float64, device=dev) for p in plans]
-    batch = fwi.Batch(plans)
+        groups.setdefault((wl.nx, wl.ny, wl.nz), []).append(wl)
+    tuned = {}
+    for key, g in groups.items():       # one schedule per grid size, chosen by the autotuner
+        tuned[key] = autotune.tune(g[0], K=len(g), steps=24, reps=3, save=False)["schedule"]
+    f32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    # grouped form: per grid, the instances are the super-shots of one per-shot-model plan
+    gplans, gcs, gws, gobs = [], [], [], []
+    for key, g in groups.items():
+        plan = fwi.Plan.from_workload(g[0], max_shots=len(g), per_shot_models=True, device=dev)
+        autotune.set_schedule(plan, tuned[key])
+        w = f32(np.stack([wl.weights[0] for wl in g]))
+        c_true = f32(np.stack([wl.c_true for wl in g])).reshape(-1)
+        gobs.append(plan.forward(c_true, w))          # each instance's data from its own true model
+        gcs.append(f32(np.stack([wl.c_model for wl in g])).reshape(-1))
+        gws.append(w)
+        gplans.append(plan)
+    vsteps = sum(p.voxel_steps(len(g), True) for p, g in zip(gplans, groups.values()))
+    bpv_step = sum(p.voxel_steps(len(g), True) * sum(alg_bytes_per_voxel(k, key[0]) for k in fwi.KERNELS)
+                   for p, g, key in zip(gplans, groups.values(), groups.keys()))
+    batch = fwi.Batch(gplans)
     t0 = time.perf_counter()
-    batch.gradient(cs, ws, obs, misfits=Ds, grads=gs)
+    batch.gradient(gcs, gws, gobs)
     torch.cuda.synchronize(dev)
     capture_s = time.perf_counter() - t0
 
@@ -255,40 +312,81 @@ def run_batch(args):
         return sum(ts) / len(ts)
 
     for _ in range(args.warmup - 1):
-        batch.gradient(cs, ws, obs, misfits=Ds, grads=gs)
-    ms_graph = timed(lambda: batch.gradient(cs, ws, obs, misfits=Ds, grads=gs), args.steps)
+        batch.gradient(gcs, gws, gobs)
+    with ClockSampler(0) as clk:
+        ms_graph = timed(lambda: batch.gradient(gcs, gws, gobs), args.steps)
+    nodes_grouped = batch.nodes()
+    assert all(p.status() == fwi.FWI_OK for p in gplans)
+
+    def grouped_sequential():
+        for p, c, w, o in zip(gplans, gcs, gws, gobs):
+            p.gradient(c, w, o)
+    grouped_sequential()
+    ms_gseq = timed(grouped_sequential, 1)
+    del batch
+    for p in gplans:
+        p.close()
+    # one single-instance plan per instance: in one graph, one after another, plain
+    plans, cs, ws, obs = [], [], [], []
+    for wl in wls:
+        plan = fwi.Plan.from_workload(wl, max_shots=1, device=dev)
+        autotune.set_schedule(plan, dict(tuned[(wl.nx, wl.ny, wl.nz)], stream_groups=1))
+        w = f32(wl.weights)
+        obs.append(plan.forward(f32(wl.c_true).reshape(-1), w))
+        plans.append(plan)
+        cs.append(f32(wl.c_model).reshape(-1))
+        ws.append(w)
+    batch1 = fwi.Batch(plans)
+    batch1.gradient(cs, ws, obs)
+    ms_graph1 = timed(lambda: batch1.gradient(cs, ws, obs), 1)
+    nodes_single = batch1.nodes()
 
     def sequential():
-        for p, c, w, o, D, g in zip(plans, cs, ws, obs, Ds, gs):
-            p.gradient(c, w, o, misfit=D, grad=g)
+        for p, c, w, o in zip(plans, cs, ws, obs):
+            p.gradient(c, w, o)
     sequential()
     ms_seq = timed(sequential, 1)
+    del batch1
     for p in plans:
         p.close()
     plains = [fwi.Plan.from_workload(wl, max_shots=1, sims_per_launch=1, device=dev) for wl in wls]
     for p, wl in zip(plains, wls):
-        autotune.set_schedule(p, tuned[(wl.nx, wl.ny, wl.nz)])
+        autotune.set_schedule(p, dict(tuned[(wl.nx, wl.ny, wl.nz)], stream_groups=1))
 
     def plain():
-        for p, c, w, o, D, g in zip(plains, cs, ws, obs, Ds, gs):
-            p.gradient(c, w, o, misfit=D, grad=g)
+        for p, c, w, o in zip(plains, cs, ws, obs):
+            p.gradient(c, w, o)
     plain()
     ms_plain = timed(plain, 1)
     G = lambda ms: vsteps / (ms / 1e3) / 1e9
+    hbm, kind = peaks()
+    step_gbs = bpv_step / (ms_graph / 1e3) / 1e9
     out = {"metric": METRIC, "value": G(ms_graph), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "batching: 16 encoded gradients of uneven grids (4 each of 64^3, "
-                                  "96x96x48, 128x128x64, 160x160x80), 1200-2000 steps, one captured graph",
-                      "voxel_steps_per_step": vsteps, "graph_nodes": batch.nodes(),
+                                  "96x96x48, 128x128x64, 160x160x80), 1200-2000 steps, grouped by grid into "
+                                  "four per-shot-model plans captured as one graph",
+                      "voxel_steps_per_step": vsteps, "graph_nodes": nodes_grouped,
                       "schedules": {"x".join(map(str, k)): v for k, v in tuned.items()},
                       "capture_and_first_run_s": capture_s},
            "gradients_per_h": 3600.0 * 16 / (ms_graph / 1e3),
+           "roofline": {"bound": "hbm", "kernel": "whole step (all four step kernels)",
+                        "achieved": step_gbs, "peak": hbm, "peak_kind": kind, "unit": "GB/s",
+                        "frac": step_gbs / hbm, "traffic": None,
+                        "alg_bytes_per_voxel_step": bpv_step / vsteps,
+                        "note": "algorithmic bytes of every step kernel of every instance over the graph time"},
+           "grouped_sequential": {"value": G(ms_gseq), "ms_per_step": ms_gseq,
+                                  "form": "the four grouped plans one after another"},
+           "single_instance_graph": {"value": G(ms_graph1), "ms_per_step": ms_graph1, "graph_nodes": nodes_single,
+                                     "form": "16 single-instance plans captured as one graph"},
            "sequential": {"value": G(ms_seq), "ms_per_step": ms_seq,
-                          "gradients_per_h": 3600.0 * 16 / (ms_seq / 1e3)},
+                          "gradients_per_h": 3600.0 * 16 / (ms_seq / 1e3),
+                          "form": "16 single-instance plans one after another"},
            "plain": {"value": G(ms_plain), "ms_per_step": ms_plain,
                      "gradients_per_h": 3600.0 * 16 / (ms_plain / 1e3),
-                     "form": "one simulation per launch sequence, instances one after another"}}
+                     "form": "one simulation per launch sequence, instances one after another"},
+           "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 
 
@@ -317,34 +415,62 @@ def run_serve(args):
     warm = [serve.Request(-1 - i, nm, kind, np.eye(8)[0], 0.0)
             for i, (nm, kind) in enumerate([(n, k) for n in names[:2] for k in ("forward", "gradient")] * 2)]
     server.run(warm, realtime=False)
-    reqs = serve.poisson_stream(names, [128, 128, 32], args.requests, args.rate, 8, seed=1000)
-    with ClockSampler(0) as clk:
-        out = server.run(reqs, realtime=True)
-    stats = out["stats"]
-    res = out["results"]
-    assert all(p.status() == fwi.FWI_OK for slots in server.pool.values() for p in [s.plan for s in slots])
-    per = {}
-    for nm in names:
-        for kind in ("forward", "gradient"):
-            lat = [r.latency for r in res if r.level == nm and r.kind == kind]
-            svc = [r.done - r.admitted for r in res if r.level == nm and r.kind == kind]
-            if lat:
-                per[f"{nm}-{kind}"] = {"n": len(lat), "p50_s": float(np.percentile(lat, 50)),
-                                       "p99_s": float(np.percentile(lat, 99)),
-                                       "median_in_service_s": float(np.median(svc))}
+    hbm, kind = peaks()
+
+    def serve_stream(n, rate, seed):
+        reqs = serve.poisson_stream(names, [128, 128, 32], n, rate, 8, seed=seed, stratified=True)
+        with ClockSampler(0) as clk:
+            out = server.run(reqs, realtime=True)
+        st, res = out["stats"], out["results"]
+        assert all(p.status() == fwi.FWI_OK for slots in server.pool.values() for p in [s.plan for s in slots])
+        per = {}
+        for nm in names:
+            for kind_ in ("forward", "gradient"):
+                lat = [r.latency for r in res if r.level == nm and r.kind == kind_]
+                svc = [r.done - r.admitted for r in res if r.level == nm and r.kind == kind_]
+                if lat:
+                    per[f"{nm}-{kind_}"] = {"n": len(lat), "p50_s": float(np.percentile(lat, 50)),
+                                            "p99_s": float(np.percentile(lat, 99)),
+                                            "median_in_service_s": float(np.median(svc))}
+        gvs = st["gvoxel_steps_per_s"]
+        # HBM fraction of the achieved rate under two byte models per voxel-step: the whole-plane
+        # two-pass kernels' 125 B and the 52 B state floor (v, rho read + written, c0 read)
+        st["hbm_frac"] = {"at_125B_per_voxel_step": gvs * 125.125 / hbm, "at_52B_state_floor": gvs * 52.0 / hbm,
+                          "peak_gbs": hbm, "peak_kind": kind}
+        return st, per, clk.summary()
+
+    stats, per, clocks = serve_stream(args.requests, args.rate, 1000)
+    sweep = []
+    for rate in [float(r) for r in args.rates.split(",") if r.strip()]:
+        st, pr, ck = serve_stream(args.sweep_requests, rate, 2000)
+        sweep.append({"rate_req_per_s": rate, "requests": st["requests"], "p50_s": st["p50_s"], "p99_s": st["p99_s"],
+                      "offered_req_per_s": st["offered_req_per_s"], "achieved_req_per_s": st["achieved_req_per_s"],
+                      "gvoxel_steps_per_s": st["gvoxel_steps_per_s"], "gradients_per_h": st["gradients_per_h"],
+                      "hbm_frac": st["hbm_frac"], "per_level": pr, "clocks": ck})
+    # highest swept rate the server kept up with (achieved >= 90 % of offered: no growing queue)
+    kept = [p for p in sweep if p["achieved_req_per_s"] and p["offered_req_per_s"]
+            and p["achieved_req_per_s"] >= 0.9 * p["offered_req_per_s"]]
+    sustainable = max(kept, key=lambda p: p["rate_req_per_s"]) if kept else None
     grid = {nm: [lv.wl.nx, lv.wl.ny, lv.wl.nz, lv.wl.nt] for nm, lv in zip(names, levels)}
     line = {"metric": METRIC, "value": stats["gvoxel_steps_per_s"], "unit": UNIT, "n_gpus": 1,
-            "steps": len(res), "warmup": len(warm), "ms_per_step": 1e3 * stats["wall_s"] / max(len(res), 1),
+            "steps": stats["requests"], "warmup": len(warm),
+            "ms_per_step": 1e3 * stats["wall_s"] / max(stats["requests"], 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "impl": "ours",
             "config": {"workload": "serving: Poisson stream of forward/gradient requests over multigrid "
                                    "levels 135x135x96, 243x243x135, 480x480x256 (PML incl.)",
                        "levels": grid, "requests": args.requests, "rate_req_per_s": args.rate,
-                       "level_mix": [128, 128, 32], "p_gradient": 0.5, "emitters_per_request": "2..8",
+                       "level_mix": [128, 128, 32], "level_mix_drawn": "stratified (exact counts, seeded order)",
+                       "p_gradient": 0.5, "emitters_per_request": "2..8",
                        "max_inflight": args.inflight, "raw_data_generation_s": t_data},
             "latency_s": {"p50": stats["p50_s"], "p99": stats["p99_s"]},
             "gradients_per_h": stats["gradients_per_h"], "serve_stats": stats, "per_level": per,
-            "clocks": clk.summary()}
+            "rate_sweep": sweep,
+            "sustainable": ({"rate_req_per_s": sustainable["rate_req_per_s"], "p50_s": sustainable["p50_s"],
+                             "p99_s": sustainable["p99_s"], "gvoxel_steps_per_s": sustainable["gvoxel_steps_per_s"],
+                             "rule": "highest swept rate with achieved >= 0.9 x offered requests/s"}
+                            if sustainable else None),
+            "clocks": clocks}
     print(json.dumps(line), flush=True)
     server.close()
 
@@ -358,21 +484,27 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--tr-box-steps", type=int, default=2,
+                    help="gradients timed with the TR re-simulation on a box enclosing Gamma (0: skip)")
     ap.add_argument("--nt", type=int, default=0,
                     help="override the number of time samples (small profiling cases only)")
     ap.add_argument("--schedule", default="",
                     help="fixed FFT schedule 'specialized,radix_order,z_tile,split_plane' instead of "
                          "autotuning (reproducible launch sequences for profiling)")
-    ap.add_argument("--requests", type=int, default=64, help="serve: length of the request stream")
+    ap.add_argument("--requests", type=int, default=256, help="serve: length of the request stream")
+    ap.add_argument("--rates", default="", help="serve: comma-separated arrival rates of a rate sweep")
+    ap.add_argument("--sweep-requests", type=int, default=32, help="serve: requests per sweep point")
     ap.add_argument("--rate", type=float, default=4.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--inflight", type=int, default=8, help="serve: admitted requests at most")
     ap.add_argument("--level", type=int, default=2, help="level: serving grid (0, 1, 2)")
     ap.add_argument("--pz", type=int, default=0, help="level: physical z extent override (profiling)")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve", "level"],
+    ap.add_argument("--oracle-runs", type=int, default=3, help="oracle: whole oracle gradients per config")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve", "level", "oracle"],
                     help="plain: the 128x128x64 gradient (the reported line); batch: the 16-instance "
                          "uneven-grid configuration as one captured graph vs sequential forms; "
                          "serve: the Poisson request stream over the three multigrid levels; "
-                         "level: one gradient (one super-shot) on a serving grid")
+                         "level: one gradient (one super-shot) on a serving grid; oracle: whole FP64 "
+                         "oracle gradients of the 32^3 and 96x96x48 configurations beside the GPU's")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -382,6 +514,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "oracle":
+        run_oracle_full(args)
         return
 
     import torch
@@ -498,21 +633,31 @@ def main():
         i_ach = bpv * wl.n_vox * i_sims / (i_ms / 1e3) / 1e9
         iso = {"achieved": i_ach, "frac": i_ach / hbm, "avg_launch_ms": i_ms / max(i_launches, 1),
                "sims_per_launch": i_sims / max(i_launches, 1), "stream_groups": 1}
-    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm,
-                "peak_kind": kind, "unit": "GB/s", "frac": achieved / hbm if achieved else None,
-                "traffic": traffic_per_launch(dominant, (wl.nx, wl.ny, wl.nz), schedule,
-                                              kern_sims / max(kern_launches, 1)),
-                "traffic_note": ("ncu DRAM read + write bytes per simulation of this kernel, times the "
-                                 "simulations per timed launch; null unless the kernels, grid and schedule "
-                                 "are those of the capture"),
-                "alg_bytes_per_launch": bpv * wl.n_vox * kern_sims / max(kern_launches, 1),
+    if iso is None:                # one stream group already: the timed launches are the kernel's own
+        iso = {"achieved": achieved, "frac": achieved / hbm if achieved else None,
+               "avg_launch_ms": kern_ms / max(kern_launches, 1),
+               "sims_per_launch": kern_sims / max(kern_launches, 1), "stream_groups": 1}
+    iso_sched = dict(schedule, stream_groups=1)
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": iso["achieved"], "peak": hbm,
+                "peak_kind": kind, "unit": "GB/s", "frac": iso["frac"],
+                "traffic": traffic_per_launch(dominant, (wl.nx, wl.ny, wl.nz), iso_sched, iso["sims_per_launch"]),
+                "traffic_note": ("ncu DRAM read + write bytes per simulation of this kernel over consecutive "
+                                 "launches of one gradient with one stream group, L2 not flushed between "
+                                 "launches (write-backs land where the hardware does them), times the "
+                                 "simulations per launch; null unless the kernels, grid and schedule are "
+                                 "those of the capture"),
+                "alg_bytes_per_launch": bpv * wl.n_vox * iso["sims_per_launch"],
                 "alg_bytes_per_voxel": bpv,
-                "step": {"alg_bytes_per_voxel_step": step_bpv, "achieved": step_gbs, "frac": step_gbs / hbm},
-                "isolated": iso,
-                "note": ("achieved/frac: the kernel's CUDA-event time over the timed region, where its "
-                         "launches overlap the other stream groups' kernels; isolated: the same kernel "
-                         "with one stream group; step: all kernels' algorithmic bytes over the step time"),
-                "avg_launch_ms": kern_ms / max(kern_launches, 1), "launches_timed": kern_launches,
+                "avg_launch_ms": iso["avg_launch_ms"], "sims_per_launch": iso["sims_per_launch"],
+                "measured_as": ("CUDA events on the kernel's stream around each of its launches in one "
+                                "gradient with one stream group (every simulation of a phase in each "
+                                "launch, no other kernel running beside it)"),
+                "overlapped": {"achieved": achieved, "frac": achieved / hbm if achieved else None,
+                               "avg_launch_ms": kern_ms / max(kern_launches, 1), "launches_timed": kern_launches,
+                               "note": ("the same kernel's CUDA-event time over the timed region, where its "
+                                        "launches overlap the other stream groups' kernels")},
+                "step": {"alg_bytes_per_voxel_step": step_bpv, "achieved": step_gbs, "frac": step_gbs / hbm,
+                         "note": "all four kernels' algorithmic bytes per voxel-step over the whole step time"},
                 "kernel_share_of_step": {k: v / sum(share_ms.values()) for k, v in share_ms.items()}}
 
     # plain form: one simulation per launch sequence, same work
@@ -538,6 +683,36 @@ def main():
                          "(sims_per_launch = 1, one stream group)"}
         pplan.close()
         del pplan
+
+    # TR re-simulation restricted to a box enclosing Gamma (Sec. 3.1): the same gradient with
+    # its TR simulations on a 96 x 96 x 64 box (margin 8, PML 8 inside the box)
+    trbox = None
+    if args.tr_box_steps > 0 and args.workload == "plain" and not args.nt:
+        box = synth.tr_box(wl, 8, 8, sizes=(32, 48, 64, 80, 96, 128))
+        bplan = fwi.Plan.from_workload(wl, pairing="literal", max_shots=K, device=dev, tr_box=box)
+        autotune.set_schedule(bplan, schedule)
+        bplan.gradient(c_model, w, observed, misfit=misfit, grad=grad)
+        torch.cuda.synchronize(dev)
+        bt = []
+        for i in range(args.tr_box_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bplan.gradient(c_model, w, observed, misfit=misfit, grad=grad)
+            b.record(stream)
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            bt.append(a.elapsed_time(b))
+        assert bplan.status() == fwi.FWI_OK
+        bms = sum(bt) / len(bt)
+        bvs = bplan.voxel_steps(K, True)
+        trbox = {"value": bvs / (bms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": bms,
+                 "gradients_per_h": 3600.0 / (bms / 1e3), "voxel_steps_per_step": bvs,
+                 "box": {"origin": list(box[0]), "size": list(box[1]), "pml": list(box[2])},
+                 "gradient_speedup": (tot_ms / args.steps) / bms,
+                 "form": ("TR simulations on a box enclosing Gamma (Sec. 3.1), adjoint and forward on the "
+                          "whole grid; oracle parity with the same box in tests/test_gpu_tr_box.py")}
+        bplan.close()
+        del bplan
 
     # end to end through the public API with host buffers (pinned), copies inside
     e2e = None
@@ -589,6 +764,7 @@ def main():
         "plain": plain,
         "batched_vs_plain": (value / plain["value"]) if plain else None,
         "e2e": e2e,
+        "tr_box": trbox,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,
