@@ -112,22 +112,6 @@ __device__ __forceinline__ void p2_fetch_rows(float2* Gb, const float* __restric
   cp_async_commit();
 }
 
-// the NY staged rows of G (padded layout of p2_fetch_rows) -> a global field plane, 16-byte
-// stores, consecutive threads on consecutive 16-byte pieces of a row
-template <class G>
-__device__ __forceinline__ void p2_store_rows(const float2* Gb, float* __restrict__ dst) {
-  constexpr int per_row = G::NXc / 4;
-  const float* d = reinterpret_cast<const float*>(Gb);
-  for (int i = threadIdx.x; i < G::NYc * per_row; i += G::NT) {
-    const int y = i / per_row, c = i - y * per_row;
-    *reinterpret_cast<float4*>(dst + y * G::NXc + 4 * c) = *reinterpret_cast<const float4*>(d + G::row_off(y) + 4 * c);
-  }
-}
-
-#ifndef P2_STORE_PASS
-#define P2_STORE_PASS 1
-#endif
-
 #ifndef P2_STAGE_STATE
 #define P2_STAGE_STATE 1
 #endif
@@ -353,9 +337,7 @@ __device__ __forceinline__ float old_value(const float* p) {
 
 // phase 4, momentum: derivative of both rows in registers, v_comp update in place
 // (Lambda^s (Lambda^s v - dt/rho0 d+ p)), then forward x step A of the new v -> out
-// SPASS: the new values overwrite the staged old ones (rows in shared memory) instead of
-// going to global memory; p2_store_rows then writes the rows out with 16-byte stores.
-template <class G, bool GIN, bool SPASS = false>
+template <class G, bool GIN>
 __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, const float2* twxT,
                                               float* __restrict__ v, const float* vin,
                                               const float* __restrict__ lam, int comp, float lz, float dtr,
@@ -399,13 +381,11 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
       if constexpr (PRE) { o0v = s0[k2]; o1v = s1[k2]; }
       else { o0v = old_value<GIN>(&i0[G::AX1 * k2]); o1v = has1 ? old_value<GIN>(&i1[G::AX1 * k2]) : 0.f; }
       const float n0 = a0 * (a0 * o0v - dtr * z[k2].x);
-      if constexpr (SPASS) const_cast<float*>(i0)[G::AX1 * k2] = n0;
-      else v0p[G::AX1 * k2] = n0;
+      v0p[G::AX1 * k2] = n0;
       float n1 = 0.f;
       if (has1) {
         n1 = a1 * (a1 * o1v - dtr * z[k2].y);
-        if constexpr (SPASS) const_cast<float*>(i1)[G::AX1 * k2] = n1;
-        else v1p[G::AX1 * k2] = n1;
+        v1p[G::AX1 * k2] = n1;
       }
       z[k2] = make_float2(n0, n1);
     });
@@ -416,7 +396,7 @@ __device__ __forceinline__ void p2_mom_update(const float2* S, float2* out, cons
 // phase 4, mass: rho_comp <- Lambda (Lambda rho - dt rho0 d- v); for the last
 // component the new rho_y is also written as pairs to pout, where p2_assemble_p turns
 // it into p = c0^2 (rho_x + rho_y + rho_z).
-template <class G, bool LAST, bool GIN, bool SPASS = false>
+template <class G, bool LAST, bool GIN>
 __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, float* __restrict__ rho,
                                                const float* rin, const float* __restrict__ lam,
                                                int comp, float lz, float dtr0, int nyl) {
@@ -457,13 +437,11 @@ __device__ __forceinline__ void p2_mass_update(const float2* S, float2* pout, fl
       if constexpr (PRE) { o0v = s0[k2]; o1v = s1[k2]; }
       else { o0v = old_value<GIN>(&i0[xo]); o1v = has1 ? old_value<GIN>(&i1[xo]) : 0.f; }
       const float r0 = a0 * (a0 * o0v - dtr0 * z[k2].x);
-      if constexpr (SPASS) const_cast<float*>(i0)[xo] = r0;
-      else rho[o0 + xo] = r0;
+      rho[o0 + xo] = r0;
       float r1 = 0.f;
       if (has1) {
         r1 = a1 * (a1 * o1v - dtr0 * z[k2].y);
-        if constexpr (SPASS) const_cast<float*>(i1)[xo] = r1;
-        else rho[o1 + xo] = r1;
+        rho[o1 + xo] = r1;
       }
       if (LAST) po[xo] = make_float2(r0, r1);
     });
@@ -599,22 +577,14 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mom(const __gr
     p2_xinv_a<G>(X, S, twx);
     if constexpr (SS) cp_async_wait_all();
     __syncthreads();
-    constexpr bool SP = SS && P2_STORE_PASS;
-    p2_mom_update<G, !SS, SP>(S, X, twxT, vg, SS ? reinterpret_cast<const float*>(Gb) : vg, P.lams[comp], comp,
-                              lz, P.dt_over_rho0, NY);
+    p2_mom_update<G, !SS>(S, X, twxT, vg, SS ? reinterpret_cast<const float*>(Gb) : vg, P.lams[comp], comp, lz,
+                          P.dt_over_rho0, NY);
     __syncthreads();
-    if constexpr (SP) {                              // new v rows out; the next spectrum overlaps 6-7
-      p2_xfwd_b<G>(X, S);
-      p2_store_rows<G>(Gb, vg);
-      __syncthreads();
+    if constexpr (G::STAGE) {                        // next spectrum overlaps phases 5-7
       if (cc < 2) p2_fetch_spec<G>(Gb, src_of(comp_of(cc + 1)));
-    } else {
-      if constexpr (G::STAGE) {                      // next spectrum overlaps phases 5-7
-        if (cc < 2) p2_fetch_spec<G>(Gb, src_of(comp_of(cc + 1)));
-      }
-      p2_xfwd_b<G>(X, S);
-      __syncthreads();
     }
+    p2_xfwd_b<G>(X, S);
+    __syncthreads();
     p2_yfwd_a<G>(S, X, twy);
     if constexpr (G::STAGE) cp_async_wait_all();
     __syncthreads();
@@ -648,8 +618,6 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
   if constexpr (G::STAGE) p2_fetch_spec<G>(Gb, Q.spec[2] + soff);
   p2_stage_twiddles<G>(sm2, P);
   constexpr bool SS = G::STAGE && P2_STAGE_STATE;
-  constexpr bool SP = SS && P2_STORE_PASS;           // new rho rows leave through the staged rows
-  float* rprev = nullptr;                            // component whose new rows wait in Gb
 #pragma unroll 1
   for (int cc = 0; cc < 3; ++cc) {
     const int comp = cc == 0 ? 0 : (cc == 1 ? 2 : 1);
@@ -658,9 +626,6 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
     cp_async_wait_all();
     __syncthreads();
     p2_yinv_a<G>(S, src, comp == 2 ? 0 : (comp == 0 ? 1 : 2), P.am[comp], twy);
-    if constexpr (SP) {
-      if (cc > 0) p2_store_rows<G>(Gb, rprev);
-    }
     __syncthreads();
     if constexpr (SS) p2_fetch_rows<G>(Gb, rg);      // overlaps phases 2 and 3
     p2_y_b<G, true>(S, X, nullptr);
@@ -671,14 +636,12 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
     const float* rin = SS ? reinterpret_cast<const float*>(Gb) : rg;
     if (cc < 2) {
       p2_fetch_spec<G>(X, (cc == 0 ? Q.spec[1] : Q.spec[0]) + soff);   // overlaps phase 4
-      p2_mass_update<G, false, !SS, SP>(S, nullptr, rg, rin, P.lam[comp], comp, lz, P.dt_rho0, NY);
+      p2_mass_update<G, false, !SS>(S, nullptr, rg, rin, P.lam[comp], comp, lz, P.dt_rho0, NY);
     } else {
-      p2_mass_update<G, true, !SS, SP>(S, X, rg, rin, P.lam[1], 1, lz, P.dt_rho0, NY);
+      p2_mass_update<G, true, !SS>(S, X, rg, rin, P.lam[1], 1, lz, P.dt_rho0, NY);
     }
-    rprev = rg;
   }
   __syncthreads();
-  if constexpr (SP) p2_store_rows<G>(Gb, rprev);
   p2_assemble_p<G>(X, Q.rho[0] + voff, Q.rho[2] + voff, c2_of(P, Q) + voff, NY);
   __syncthreads();
   // sparse updates of rho_xi and p on this plane, then recording
