@@ -40,21 +40,21 @@ def alg_bytes_per_voxel(kernel, nx):
             "plane_mass": 4 * hf + 28.0}[kernel]  # 3 spectra read, P_xy written; rho r/w; c0^2
 
 
-# DRAM bytes per simulation in one launch, read + write, from ncu on the 128x128x64 gradient
-# (launches of one simulation in the forward phase, four stream groups, schedule
-# specialized 2 / z_tile 32 / split_plane 0; ncu replays each launch serialised from a cold
-# L2, and the writes, which stay in the 126 MB L2 until the next kernel, count as ~0).
-# The command and the per-kernel table are in profiles/step_kernels_128x128x64_gradient.md.
-# Valid only for these kernels at this size and schedule; anything else reports null.
-# Each kernel's launches depend only on the knobs listed for it (the plane kernels do not
-# see z_tile, the z passes do not see split_plane).
+# DRAM bytes per simulation in one launch, read + write, from ncu on the 128x128x64 gradient:
+# every launch of one gradient (40 time steps, one stream group: 4 simulations per launch in
+# the forward phase, 8 in the backward phase), L2 not flushed between launches, so write-backs
+# are counted where the hardware performs them (often in the next kernel's launch).  The
+# command and the per-kernel table are in profiles/step_kernels_128x128x64_gradient.md.  Valid
+# only for these kernels at this size and schedule; anything else reports null.  Each kernel's
+# launches depend only on the knobs listed for it (the plane kernels do not see z_tile, the z
+# passes do not see split_plane).
 TRAFFIC_PER_SIM = {"grid": (128, 128, 64),
-                   "knobs": {"zpass_momentum": {"specialized": 2, "z_tile": 32},
-                             "zpass_mass": {"specialized": 2, "z_tile": 32},
-                             "plane_momentum": {"specialized": 2, "split_plane": 0},
-                             "plane_mass": {"specialized": 2, "split_plane": 0}},
-                   "bytes": {"zpass_momentum": 4.30e6, "plane_momentum": 21.15e6,
-                             "zpass_mass": 12.82e6, "plane_mass": 29.65e6}}
+                   "knobs": {"zpass_momentum": {"specialized": 2, "z_tile": 32, "stream_groups": 1},
+                             "zpass_mass": {"specialized": 2, "z_tile": 32, "stream_groups": 1},
+                             "plane_momentum": {"specialized": 2, "split_plane": 0, "stream_groups": 1},
+                             "plane_mass": {"specialized": 2, "split_plane": 0, "stream_groups": 1}},
+                   "bytes": {"zpass_momentum": 7.89e6, "plane_momentum": 39.83e6,
+                             "zpass_mass": 18.78e6, "plane_mass": 40.04e6}}
 
 
 def traffic_per_launch(kernel, grid, schedule, sims_per_launch):

@@ -32,9 +32,12 @@ def test_algorithmic_bytes_count_fields_and_half_spectra(bench):
 
 
 def test_traffic_only_for_the_captured_launches(bench):
-    sched = {"specialized": 2, "radix_order": 0, "z_tile": 32, "split_plane": 0, "stream_groups": 4}
+    # the capture ran one stream group (every simulation of a phase in each launch), the launch
+    # shape the headline roofline times
+    sched = {"specialized": 2, "radix_order": 0, "z_tile": 32, "split_plane": 0, "stream_groups": 1}
     per_sim = bench.TRAFFIC_PER_SIM["bytes"]["plane_mass"]
-    assert bench.traffic_per_launch("plane_mass", (128, 128, 64), sched, 1.5) == pytest.approx(1.5 * per_sim)
+    assert bench.traffic_per_launch("plane_mass", (128, 128, 64), sched, 6.0) == pytest.approx(6.0 * per_sim)
+    assert bench.traffic_per_launch("plane_mass", (128, 128, 64), dict(sched, stream_groups=4), 1.5) is None
     # the plane kernels do not see the z tile; the z passes do
     z16 = dict(sched, z_tile=16)
     assert bench.traffic_per_launch("plane_mass", (128, 128, 64), z16, 1.0) == pytest.approx(per_sim)
