@@ -1515,6 +1515,7 @@ struct fwi_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<uintptr_t> key;     // arguments the graph was captured with
   int64_t nodes = 0;
+  int branches = 0;               // concurrent chains of plans (0: one per plan)
 };
 
 fwi_status fwi_batch_create(int32_t n, fwi_plan* const* plans, fwi_batch** out) {
@@ -1564,12 +1565,15 @@ fwi_status fwi_batch_gradient(fwi_batch* b, const float* const* c, const float* 
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     fwi_status s = FWI_OK;
     if (cudaEventRecord(b->fork, cs) != cudaSuccess) s = FWI_ECUDA;
-    for (int i = 0; i < n && s == FWI_OK; ++i) {
-      if (cudaStreamWaitEvent(b->side[i], b->fork, 0) != cudaSuccess) { s = FWI_ECUDA; break; }
-      s = fwi_gradient(b->plans[i], c[i], w[i], K[i], observed[i], observed_encoded[i], misfit[i], grad[i],
-                       nullptr, b->side[i]);
-      if (s == FWI_OK && cudaEventRecord(b->join[i], b->side[i]) != cudaSuccess) s = FWI_ECUDA;
-      if (s == FWI_OK && cudaStreamWaitEvent(cs, b->join[i], 0) != cudaSuccess) s = FWI_ECUDA;
+    // chain h runs plans [h n / B, (h + 1) n / B) one after another on side stream h
+    const int B = b->branches > 0 ? std::min(b->branches, n) : n;
+    for (int h = 0; h < B && s == FWI_OK; ++h) {
+      if (cudaStreamWaitEvent(b->side[h], b->fork, 0) != cudaSuccess) { s = FWI_ECUDA; break; }
+      for (int i = h * n / B; i < (h + 1) * n / B && s == FWI_OK; ++i)
+        s = fwi_gradient(b->plans[i], c[i], w[i], K[i], observed[i], observed_encoded[i], misfit[i], grad[i],
+                         nullptr, b->side[h]);
+      if (s == FWI_OK && cudaEventRecord(b->join[h], b->side[h]) != cudaSuccess) s = FWI_ECUDA;
+      if (s == FWI_OK && cudaStreamWaitEvent(cs, b->join[h], 0) != cudaSuccess) s = FWI_ECUDA;
     }
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &g);
@@ -1597,6 +1601,17 @@ fwi_status fwi_batch_gradient(fwi_batch* b, const float* const* c, const float* 
 }
 
 int64_t fwi_batch_nodes(const fwi_batch* b) { return b ? b->nodes : -1; }
+
+fwi_status fwi_batch_set_branches(fwi_batch* b, int32_t branches) {
+  if (!b || branches < 0) return FWI_EINVAL;
+  if (branches != b->branches && b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->key.clear();
+  }
+  b->branches = branches;
+  return FWI_OK;
+}
 
 fwi_status fwi_batch_destroy(fwi_batch* b) {
   if (!b) return FWI_OK;

@@ -94,7 +94,8 @@ def test_instance_with_its_own_model_matches_the_oracle():
 
 def test_batch_of_instance_plans_equals_separate_calls():
     """Two grids, two instances each, in one captured graph: every instance's misfit and
-    gradient equal the per-plan calls bit for bit, on two replays."""
+    gradient equal the per-plan calls bit for bit, on a replay and with the plans side by side
+    or in one chain."""
     cases = [_instances((24, 20, 18), 60, 7), _instances((20, 20, 16), 60, 9)]
     plans, cs, ws, obs = [], [], [], []
     for wl, models, _, f_obs in cases:
@@ -105,7 +106,8 @@ def test_batch_of_instance_plans_equals_separate_calls():
     ref = [p.gradient(c, w, o) for p, c, w, o in zip(plans, cs, ws, obs)]
     ref = [(D.clone(), g.clone()) for D, g in ref]
     batch = fwi.Batch(plans)
-    for _ in range(2):
+    for branches in (0, 0, 1, 2):            # capture, replay, then the plans in one and two chains
+        batch.set_branches(branches)
         Ds, gs = batch.gradient(cs, ws, obs)
         torch.cuda.synchronize()
         for (D0, g0), D1, g1 in zip(ref, Ds, gs):
