@@ -1405,7 +1405,7 @@ int64_t fwi_plan_launches(const fwi_plan* p, int32_t K, int32_t gradient) {
   };
   const fwi_plan* tp = p->tr ? p->tr : p;
   const int G = group_count(p, K), KG = (K + G - 1) / G;
-  int64_t n = 2 + 1;                                    // prepare x2, source amplitudes
+  int64_t n = 2 * p->models + 1;                        // prepare x2 per model, source amplitudes
   for (int g = 0; g < G; ++g) {                         // forward steps (groups with shots)
     const int ng = std::min(K, (g + 1) * KG) - g * KG;
     if (ng > 0) n += nt * step(p, ng);
@@ -1413,7 +1413,7 @@ int64_t fwi_plan_launches(const fwi_plan* p, int32_t K, int32_t gradient) {
   if (gradient) {
     const bool exact = p->prob.pairing == FWI_PAIRING_EXACT;
     const int64_t nit = exact ? Nt + 1 : Nt - 1;
-    if (p->tr) n += 1 + 2;                              // crop, prepare of the box
+    if (p->tr) n += 3 * p->models;                      // crop and prepare of the box, per model
     n += 2 + (tp->split ? 2 : 1) + step(tp, K);         // misfit x2, TR init, lead TR step
     const int64_t full = std::min<int64_t>(nit, Nt - 1);  // iterations with a TR step
     const int64_t acc = fused_accumulation(p) ? 0 : 1;  // k_accumulate per iteration
