@@ -135,3 +135,20 @@ def test_tr_box_validation_and_workspace(L):
     for o, s, p in bad:
         assert fwi.fwi_plan_set_tr_box(plan, o, s, p)[0] == fwi.FWI_EINVAL, (o, s, p)
     fwi.fwi_plan_destroy(plan)
+
+
+def test_per_shot_models_validation_and_workspace(L):
+    """per_shot_models = 1 keeps one c0^2 field and one set of sparse coefficients per
+    super-shot (K of them); any other value than 0 or 1 is rejected."""
+    wl = synth.small_workload(24, 20, 18, 40)
+    P, keep = _problem(wl)
+    st, plan, one = fwi.fwi_plan_create(P)
+    assert st == fwi.FWI_OK
+    fwi.fwi_plan_destroy(plan)
+    P, keep = _problem(wl, per_shot_models=1)
+    st, plan, each = fwi.fwi_plan_create(P)
+    assert st == fwi.FWI_OK
+    assert each - one >= (P.max_shots - 1) * wl.n_vox * 4      # the extra c0^2 fields at least
+    fwi.fwi_plan_destroy(plan)
+    P, keep = _problem(wl, per_shot_models=2)
+    assert fwi.fwi_plan_create(P)[0] == fwi.FWI_EINVAL
