@@ -515,11 +515,13 @@ def main():
     ap.add_argument("--level", type=int, default=2, help="level: serving grid (0, 1, 2)")
     ap.add_argument("--pz", type=int, default=0, help="level: physical z extent override (profiling)")
     ap.add_argument("--oracle-runs", type=int, default=3, help="oracle: whole oracle gradients per config")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve", "level", "oracle"],
+    ap.add_argument("--instance", type=int, default=12, help="instance: which of the 16 uneven-grid instances")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batch", "serve", "level", "oracle", "instance"],
                     help="plain: the 128x128x64 gradient (the reported line); batch: the 16-instance "
                          "uneven-grid configuration as one captured graph vs sequential forms; "
                          "serve: the Poisson request stream over the three multigrid levels; "
-                         "level: one gradient (one super-shot) on a serving grid; oracle: whole FP64 "
+                         "level: one gradient (one super-shot) on a serving grid; instance: one gradient of "
+                         "one uneven-grid batch instance; oracle: whole FP64 "
                          "oracle gradients of the 32^3 and 96x96x48 configurations beside the GPU's")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -551,12 +553,16 @@ def main():
 
     if args.workload == "level":
         wl = synth.serving_level(args.level, n_src=8, seed=1000 + args.level, pz=args.pz or None)
+    elif args.workload == "instance":
+        wl = synth.config3_instance(args.instance)
     else:
         wl = synth.config2()
     if args.nt:
         wl.nt = args.nt
         wl.wavelet = wl.wavelet[:args.nt]
-    workload = WORKLOAD if args.workload != "level" else (
+    workload = WORKLOAD if args.workload == "plain" else (
+        f"uneven-grid batch instance {args.instance}: one TR gradient (one super-shot of 128 emitters, 512 "
+        f"receivers) on the {wl.nx}x{wl.ny}x{wl.nz} grid, {wl.nt} steps" if args.workload == "instance" else
         f"serving level {args.level}: one TR gradient (one super-shot of 8 emitters, 1024 receivers) "
         f"on the {wl.nx}x{wl.ny}x{wl.nz} grid, {wl.nt} steps")
     K = wl.weights.shape[0]
