@@ -311,15 +311,23 @@ def run_batch(args):
             ts.append(a.elapsed_time(b))
         return sum(ts) / len(ts)
 
-    # graph concurrency, chosen like an FFT schedule: the plans in 1, 2 or 4 chains side by side
-    # (the large plans fill the GPU on their own, so side by side they mostly share L2)
-    by_branches = {}
-    for nb in (1, 2, 4):
-        batch.set_branches(nb)
+    # Graph concurrency, chosen by measurement like an FFT schedule: which plans run one after
+    # another on which of the chains that run side by side.  The plans in batch order are
+    # 64^3, 96x96x48, 128x128x64, 160x160x80.  Side by side, plans that each fill the GPU mostly
+    # share L2; the largest grid's one-CTA-per-SM plane launches leave SMs idle in their last
+    # wave, which a smaller plan beside it can fill.
+    largest = max(range(len(gplans)), key=lambda i: gplans[i].n_vox)
+    arrangements = {"one chain": [0] * len(gplans),
+                    "largest beside the rest": [1 if i == largest else 0 for i in range(len(gplans))],
+                    "two mixed chains": [i % 2 for i in range(len(gplans))],
+                    "one chain per grid": list(range(len(gplans)))}
+    by_arrangement = {}
+    for name, chain in arrangements.items():
+        batch.set_chains(chain)
         batch.gradient(gcs, gws, gobs)
-        by_branches[nb] = timed(lambda: batch.gradient(gcs, gws, gobs), 1)
-    best = min(by_branches, key=by_branches.get)
-    batch.set_branches(best)
+        by_arrangement[name] = timed(lambda: batch.gradient(gcs, gws, gobs), 1)
+    best = min(by_arrangement, key=by_arrangement.get)
+    batch.set_chains(arrangements[best])
     for _ in range(args.warmup - 1):
         batch.gradient(gcs, gws, gobs)
     with ClockSampler(0) as clk:
@@ -390,8 +398,9 @@ def run_batch(args):
                         "frac": step_gbs / hbm, "traffic": None,
                         "alg_bytes_per_voxel_step": bpv_step / vsteps,
                         "note": "algorithmic bytes of every step kernel of every instance over the graph time"},
-           "graph_chains": {"chosen": best, "ms_by_chains": by_branches,
-                            "form": "the four grouped plans in 1, 2 or 4 chains side by side in the graph"},
+           "graph_chains": {"chosen": best, "chain_of_plan": arrangements[best], "ms_by_arrangement": by_arrangement,
+                            "plan_order": ["x".join(map(str, k)) for k in groups],
+                            "form": "which of the four grouped plans run one after another on which chain"},
            "grouped_sequential": {"value": G(ms_gseq), "ms_per_step": ms_gseq, "per_grid": per_grid,
                                   "form": "the four grouped plans one after another, no graph"},
            "single_instance_graph": {"value": G(ms_graph1), "ms_per_step": ms_graph1, "graph_nodes": nodes_single,

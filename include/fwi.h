@@ -384,15 +384,16 @@ fwi_status fwi_batch_gradient(fwi_batch *batch, const float *const *c, const flo
 /* Kernel launches the captured graph holds (0 before the first capture). */
 int64_t fwi_batch_nodes(const fwi_batch *batch);
 /*
- * Concurrency of the batch graph: the plans are split, in their order, into `branches`
- * contiguous chains that run side by side, each chain's plans one after another
- * (0, the default: one chain per plan; 1: all plans in sequence).  Plans that each fill
- * the GPU (several super-shots or stream groups) keep their data in L2 between their own
- * launches when they do not run side by side; small ones fill each other's idle SMs when
- * they do.  Results are identical for every value.  The next fwi_batch_gradient
- * re-captures.  Errors: FWI_EINVAL (NULL, branches < 0).
+ * Concurrency of the batch graph: plan i runs on chain chain[i] (host [n], values 0..n-1);
+ * the chains run side by side, each chain's plans one after another in batch order.
+ * chain = NULL (the default) gives every plan a chain of its own; all zeros runs the
+ * plans in sequence.  Plans that each fill the GPU (several super-shots or stream groups)
+ * keep their data in L2 between their own launches when they do not run side by side;
+ * small ones fill the SMs that a large one leaves idle when they do.  Results are identical
+ * for every assignment.  The next fwi_batch_gradient re-captures.
+ * Errors: FWI_EINVAL (NULL batch, a chain outside 0..n-1).
  */
-fwi_status fwi_batch_set_branches(fwi_batch *batch, int32_t branches);
+fwi_status fwi_batch_set_chains(fwi_batch *batch, const int32_t *chain);
 fwi_status fwi_batch_destroy(fwi_batch *batch);
 
 /* Release the plan's host memory (not the workspace, which the caller owns). */

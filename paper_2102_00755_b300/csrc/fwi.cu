@@ -1515,7 +1515,7 @@ struct fwi_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<uintptr_t> key;     // arguments the graph was captured with
   int64_t nodes = 0;
-  int branches = 0;               // concurrent chains of plans (0: one per plan)
+  std::vector<int> chain;         // chain of each plan; empty: one chain per plan
 };
 
 fwi_status fwi_batch_create(int32_t n, fwi_plan* const* plans, fwi_batch** out) {
@@ -1565,14 +1565,18 @@ fwi_status fwi_batch_gradient(fwi_batch* b, const float* const* c, const float* 
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     fwi_status s = FWI_OK;
     if (cudaEventRecord(b->fork, cs) != cudaSuccess) s = FWI_ECUDA;
-    // chain h runs plans [h n / B, (h + 1) n / B) one after another on side stream h
-    const int B = b->branches > 0 ? std::min(b->branches, n) : n;
-    for (int h = 0; h < B && s == FWI_OK; ++h) {
-      if (cudaStreamWaitEvent(b->side[h], b->fork, 0) != cudaSuccess) { s = FWI_ECUDA; break; }
-      for (int i = h * n / B; i < (h + 1) * n / B && s == FWI_OK; ++i)
+    // chain h runs its plans one after another, in batch order, on side stream h
+    for (int h = 0; h < n && s == FWI_OK; ++h) {
+      bool any = false;
+      for (int i = 0; i < n && s == FWI_OK; ++i) {
+        if ((b->chain.empty() ? i : b->chain[i]) != h) continue;
+        if (!any && cudaStreamWaitEvent(b->side[h], b->fork, 0) != cudaSuccess) { s = FWI_ECUDA; break; }
+        any = true;
         s = fwi_gradient(b->plans[i], c[i], w[i], K[i], observed[i], observed_encoded[i], misfit[i], grad[i],
                          nullptr, b->side[h]);
-      if (s == FWI_OK && cudaEventRecord(b->join[h], b->side[h]) != cudaSuccess) s = FWI_ECUDA;
+      }
+      if (!any || s != FWI_OK) continue;
+      if (cudaEventRecord(b->join[h], b->side[h]) != cudaSuccess) s = FWI_ECUDA;
       if (s == FWI_OK && cudaStreamWaitEvent(cs, b->join[h], 0) != cudaSuccess) s = FWI_ECUDA;
     }
     cudaGraph_t g = nullptr;
@@ -1602,14 +1606,21 @@ fwi_status fwi_batch_gradient(fwi_batch* b, const float* const* c, const float* 
 
 int64_t fwi_batch_nodes(const fwi_batch* b) { return b ? b->nodes : -1; }
 
-fwi_status fwi_batch_set_branches(fwi_batch* b, int32_t branches) {
-  if (!b || branches < 0) return FWI_EINVAL;
-  if (branches != b->branches && b->exec) {
+fwi_status fwi_batch_set_chains(fwi_batch* b, const int32_t* chain) {
+  if (!b) return FWI_EINVAL;
+  const int n = (int)b->plans.size();
+  std::vector<int> ch;
+  if (chain) {
+    for (int i = 0; i < n; ++i)
+      if (chain[i] < 0 || chain[i] >= n) return FWI_EINVAL;
+    ch.assign(chain, chain + n);
+  }
+  if (ch != b->chain && b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     b->key.clear();
   }
-  b->branches = branches;
+  b->chain = ch;
   return FWI_OK;
 }
 

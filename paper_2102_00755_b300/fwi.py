@@ -33,7 +33,7 @@ C_SYMBOLS = ("fwi_plan_create", "fwi_plan_set_tr_box", "fwi_plan_bind_workspace"
              "fwi_plan_status", "fwi_plan_voxel_steps", "fwi_plan_launches", "fwi_plan_profile",
              "fwi_plan_profile_read", "fwi_plan_set_schedule", "fwi_plan_get_schedule",
              "fwi_adjoint_source_noalloc", "fwi_batch_create",
-             "fwi_batch_gradient", "fwi_batch_nodes", "fwi_batch_set_branches", "fwi_batch_destroy",
+             "fwi_batch_gradient", "fwi_batch_nodes", "fwi_batch_set_chains", "fwi_batch_destroy",
              "fwi_plan_destroy",
              "fwi_status_string", "fwi_last_cuda_error", "fwi_lbfgs_create", "fwi_lbfgs_bind_workspace",
              "fwi_lbfgs_push", "fwi_lbfgs_apply", "fwi_lbfgs_size", "fwi_lbfgs_destroy", "fwi_vec_step_project",
@@ -126,8 +126,8 @@ def lib():
         L.fwi_batch_gradient.restype = ctypes.c_int
         L.fwi_batch_nodes.argtypes = [vp]
         L.fwi_batch_nodes.restype = i64
-        L.fwi_batch_set_branches.argtypes = [vp, i32]
-        L.fwi_batch_set_branches.restype = ctypes.c_int
+        L.fwi_batch_set_chains.argtypes = [vp, ctypes.POINTER(i32)]
+        L.fwi_batch_set_chains.restype = ctypes.c_int
         L.fwi_batch_destroy.argtypes = [vp]
         L.fwi_batch_destroy.restype = ctypes.c_int
         L.fwi_plan_destroy.argtypes = [vp]
@@ -580,10 +580,11 @@ class Batch:
     def nodes(self) -> int:
         return fwi_batch_nodes(self.handle)
 
-    def set_branches(self, branches: int):
-        """Plans in `branches` contiguous chains side by side (0: one per plan; see
-        fwi_batch_set_branches)."""
-        _check(lib().fwi_batch_set_branches(self.handle, int(branches)), "fwi_batch_set_branches")
+    def set_chains(self, chain=None):
+        """Plan i on chain chain[i]; chains run side by side, each chain's plans in sequence
+        (None: one chain per plan; see fwi_batch_set_chains)."""
+        arr = None if chain is None else (ctypes.c_int32 * len(self.plans))(*map(int, chain))
+        _check(lib().fwi_batch_set_chains(self.handle, arr), "fwi_batch_set_chains")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -106,8 +106,8 @@ def test_batch_of_instance_plans_equals_separate_calls():
     ref = [p.gradient(c, w, o) for p, c, w, o in zip(plans, cs, ws, obs)]
     ref = [(D.clone(), g.clone()) for D, g in ref]
     batch = fwi.Batch(plans)
-    for branches in (0, 0, 1, 2):            # capture, replay, then the plans in one and two chains
-        batch.set_branches(branches)
+    for chain in (None, None, [0, 0], [1, 0]):   # capture, replay, one chain, chains in reverse
+        batch.set_chains(chain)
         Ds, gs = batch.gradient(cs, ws, obs)
         torch.cuda.synchronize()
         for (D0, g0), D1, g1 in zip(ref, Ds, gs):
