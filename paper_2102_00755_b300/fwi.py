@@ -565,6 +565,10 @@ class Batch:
                               for p, c, w in zip(self.plans, cs, weights)])
             misfits = self._out[1] if misfits is None else misfits
             grads = self._out[2] if grads is None else grads
+        if not (len(cs) == len(weights) == len(observed) == len(encoded) == len(misfits) == len(grads) == n):
+            raise ValueError("one entry per plan expected in every argument list")
+        for p, c, w, o, e, m, g in zip(self.plans, cs, weights, observed, encoded, misfits, grads):
+            p._check_sizes(w.shape[0], c, w, grad=g, misfit=m, observed=o, encoded=e)
         st = fwi_batch_gradient(self.handle,
                                 [_dptr(c, torch.float32, "c").value for c in cs],
                                 [_dptr(w, torch.float32, "weights").value for w in weights],
