@@ -692,7 +692,8 @@ __global__ void __launch_bounds__(Plane2<NX, NY>::NT, 1) k_plane2_mass(const __g
     p2_record_gamma(P, Q, zf, role, shot, P.slot[blockIdx.y], P.gam_ptr[key0], P.gam_ptr[key1], G::NT,
                     [](int pf) { return p2_pf<G>(pf); });
   }
-  __syncthreads();
+  // the recording above only reads X, the forward x step A below reads X and writes S: they share
+  // one barrier interval
   // forward x step A of p (pairs in X) -> S, then step B, R2C unpacking and y
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
     int p, k1;

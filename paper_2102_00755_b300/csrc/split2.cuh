@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(X2<NX, NPC>::NT, 2) k_xpass2_mass(const __grid
   } else {
     p2_record_gamma(P, Q, zf, role, shot, P.slot[blockIdx.z], P.gam_ptr[key0], P.gam_ptr[key1], G::NT, loc);
   }
-  __syncthreads();
+  // the recording above only reads X; the forward x step A below reads X and writes S
   // forward x step A of p (pairs in X) -> S, then step B, R2C unpacking -> rows of spec[0]
   for (int t = threadIdx.x; t < G::T4; t += G::NT) {
     const int p = t / G::AX1, k1 = t - p * G::AX1;
