@@ -23,6 +23,7 @@ from . import oracle_cases as oc
 pytestmark = pytest.mark.gpu
 
 TOL_TRACES = 1e-4
+TOL_GRAD = 1e-3          # gradient rel l2 of FP32 fields against exact arithmetic
 NT = 100
 
 
@@ -117,3 +118,51 @@ def test_full_size_gradient_properties_largest_level():
     assert np.any(g_a[gam])
     assert oc.rel(g_ab, g_a + g_b) < 1e-4
     plan.close()
+
+
+def test_bench_configuration_full_length_gradient_properties():
+    """The timed workload itself: the 128x128x64 phantom with all 1500 steps, four super-shots,
+    in the default launch configuration (two-step kernels, stream groups).  Properties that hold
+    at any size: zero residual gives a zero misfit and gradient; the misfit is 0.5 ||q||^2 of the
+    returned traces; the gradient lives on Gamma and is linear in the residual; and it is the
+    mean over the super-shots of the per-shot gradients of the same problem run as instances."""
+    wl = synth.config2()
+    K = len(wl.weights)
+    plan = fwi.Plan.from_workload(wl, max_shots=K)
+    c = _dev(wl.c_model).reshape(-1)
+    w = _dev(wl.weights)
+    f = plan.forward(c, w).clone()
+    rng = np.random.default_rng(5)
+    scale = float(f.abs().max())
+    r_a = _dev(scale * 0.05 * rng.standard_normal(f.shape))
+    r_b = _dev(scale * 0.05 * rng.standard_normal(f.shape))
+
+    def grad(obs):
+        tr = torch.empty_like(f)
+        D, g = plan.gradient(c, w, obs, traces=tr)
+        torch.cuda.synchronize()
+        assert plan.status() == fwi.FWI_OK
+        return tr, D.cpu().numpy(), g.cpu().numpy()
+
+    tr0, D0, g0 = grad(f)
+    assert torch.equal(tr0, f)
+    assert not np.any(D0) and not np.any(g0)
+    tr_a, D_a, g_a = grad(f - r_a)
+    _, _, g_b = grad(f - r_b)
+    _, _, g_ab = grad(f - r_a - r_b)
+    res = (tr_a.double() - (f - r_a).double()).cpu().numpy()
+    assert np.all(np.abs(D_a - 0.5 * np.sum(res ** 2, axis=(1, 2))) <= 1e-9 * D_a)
+    gam = np.zeros(wl.n_vox, bool)
+    gam[wl.gamma_idx] = True
+    assert not np.any(g_a[~gam]) and np.any(g_a[gam])
+    # linear up to FP32 rounding of three 1500-step gradients: the gradient tolerance
+    assert oc.rel(g_ab, g_a + g_b) < TOL_GRAD
+    plan.close()
+    inst = fwi.Plan.from_workload(wl, max_shots=K, per_shot_models=True)
+    cs = _dev(np.stack([wl.c_model] * K)).reshape(-1)
+    D_i, g_i = inst.gradient(cs, w, f - r_a)
+    assert inst.status() == fwi.FWI_OK
+    assert np.array_equal(D_i.cpu().numpy(), D_a)
+    g_mean = g_i.cpu().numpy().reshape(K, -1).mean(axis=0)
+    assert np.abs(g_mean - g_a).max() <= 1e-12 * np.abs(g_a).max()
+    inst.close()
