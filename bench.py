@@ -53,8 +53,8 @@ TRAFFIC_PER_SIM = {"grid": (128, 128, 64),
                              "zpass_mass": {"specialized": 2, "z_tile": 32, "stream_groups": 1},
                              "plane_momentum": {"specialized": 2, "split_plane": 0, "stream_groups": 1},
                              "plane_mass": {"specialized": 2, "split_plane": 0, "stream_groups": 1}},
-                   "bytes": {"zpass_momentum": 7.89e6, "plane_momentum": 39.83e6,
-                             "zpass_mass": 18.78e6, "plane_mass": 40.04e6}}
+                   "bytes": {"zpass_momentum": 7.88e6, "plane_momentum": 39.80e6,
+                             "zpass_mass": 18.78e6, "plane_mass": 40.03e6}}
 
 
 def traffic_per_launch(kernel, grid, schedule, sims_per_launch):
