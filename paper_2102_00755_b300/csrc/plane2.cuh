@@ -38,6 +38,9 @@ namespace fwi {
 #ifndef P2_REMAP
 #define P2_REMAP 1
 #endif
+#ifndef P2_NT160
+#define P2_NT160 512
+#endif
 #ifndef P2_NT128
 #define P2_NT128 640
 #endif
@@ -59,8 +62,10 @@ struct Plane2 {
   // Threads per CTA (one CTA per SM: the plane buffers take most of shared memory).
   // Chosen per size by measurement, among counts whose registers fit 64K per SM; for
   // 128 the phases' 1040, 520, 1024 and 512 tasks take 2, 1, 2 and 1 rounds of 640
-  // threads (544 fills the rounds better but hides less latency: 0.7 % slower).
-  static constexpr int NT = NX == 128 ? P2_NT128 : NX == 135 ? 352 : NX == 160 ? 416 : NX == 96 ? 416
+  // threads (544 fills the rounds better but hides less latency: 0.7 % slower); for 160,
+  // whose planes cannot be staged, 512 threads hide more of the global loads than 416
+  // (+4.8 % on a 160 x 160 x 80 gradient) and 640 less (+0.6 %).
+  static constexpr int NT = NX == 128 ? P2_NT128 : NX == 135 ? 352 : NX == 160 ? P2_NT160 : NX == 96 ? 416
                           : NX == 64 ? 288 : 128;
   static constexpr int TW = NX + NX + NY;                 // twx, twxT, twy
   // Phase-4 task order.  Tasks (p, k1) of one half-warp read and write 64-bit words at
