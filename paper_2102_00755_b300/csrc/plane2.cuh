@@ -41,6 +41,15 @@ namespace fwi {
 #ifndef P2_NT160
 #define P2_NT160 512
 #endif
+#ifndef P2_NT135
+#define P2_NT135 352
+#endif
+#ifndef P2_NT96
+#define P2_NT96 512
+#endif
+#ifndef P2_NT64
+#define P2_NT64 288
+#endif
 #ifndef P2_NT128
 #define P2_NT128 640
 #endif
@@ -64,9 +73,10 @@ struct Plane2 {
   // 128 the phases' 1040, 520, 1024 and 512 tasks take 2, 1, 2 and 1 rounds of 640
   // threads (544 fills the rounds better but hides less latency: 0.7 % slower); for 160,
   // whose planes cannot be staged, 512 threads hide more of the global loads than 416
-  // (+4.8 % on a 160 x 160 x 80 gradient) and 640 less (+0.6 %).
-  static constexpr int NT = NX == 128 ? P2_NT128 : NX == 135 ? 352 : NX == 160 ? P2_NT160 : NX == 96 ? 416
-                          : NX == 64 ? 288 : 128;
+  // (+4.8 % on a 160 x 160 x 80 gradient) and 640 less (+0.6 %); for 96, 512 rather than
+  // 416 (+2.1 % on a 96 x 96 x 48 gradient); 135 and 64 gain nothing from 448 / 384.
+  static constexpr int NT = NX == 128 ? P2_NT128 : NX == 135 ? P2_NT135 : NX == 160 ? P2_NT160 : NX == 96 ? P2_NT96
+                          : NX == 64 ? P2_NT64 : 128;
   static constexpr int TW = NX + NX + NY;                 // twx, twxT, twy
   // Phase-4 task order.  Tasks (p, k1) of one half-warp read and write 64-bit words at
   // p PST + k1 + const in S and X; with AX1 = 8 and PST = PA = 1 (mod 16) the row pairs
