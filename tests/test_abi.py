@@ -152,3 +152,36 @@ def test_per_shot_models_validation_and_workspace(L):
     fwi.fwi_plan_destroy(plan)
     P, keep = _problem(wl, per_shot_models=2)
     assert fwi.fwi_plan_create(P)[0] == fwi.FWI_EINVAL
+
+
+def test_launch_count_follows_the_schedule(L):
+    """fwi_plan_launches (the bench's gpu_launches claim) from the host: per time step 4
+    launches per stream group (8 with split planes); the two-step kernels add the gradient
+    term inside the mass kernel, the warp-owned kernels need one accumulation launch per
+    iteration; a TR box adds its crop and preparation."""
+    import ctypes as C
+    wl = synth.small_workload(32, 32, 32, 40, pml=4, n_src=3, n_rec=24, K=4, layer=2, gamma_frac=0.25)
+    P, keep = _problem(wl, max_shots=4)
+    st, plan, _ = fwi.fwi_plan_create(P)
+    assert st == fwi.FWI_OK
+
+    def launches(**sched):
+        s = fwi.fwi_schedule(sched.get("specialized", 2), 0, 32, sched.get("split_plane", 0),
+                             sched.get("stream_groups", 1))
+        assert L.fwi_plan_set_schedule(plan, C.byref(s)) == fwi.FWI_OK
+        return fwi.fwi_plan_launches(plan, 4, 0), fwi.fwi_plan_launches(plan, 4, 1)
+
+    nt = wl.nt
+    f1, g1 = launches(stream_groups=1)
+    f4, g4 = launches(stream_groups=4)
+    assert f1 == 3 + 4 * nt and f4 == 3 + 4 * 4 * nt
+    # backward with one group: misfit x2, TR init, lead step, (nt - 2) iterations of 4, one final
+    # accumulation, the scatter (two-step kernels: no per-iteration accumulation)
+    assert g1 - f1 == 2 + 1 + 4 + 4 * (nt - 2) + 1 + 1
+    fw, gw = launches(specialized=1, stream_groups=1)          # warp-owned kernels
+    assert fw == f1 and gw - g1 == (nt - 2) - 1
+    st, _ = fwi.fwi_plan_set_tr_box(plan, *synth.tr_box(wl, 1, 2))
+    assert st == fwi.FWI_OK
+    fb, gb = launches(stream_groups=1)
+    assert fb == f1 and gb - g1 == 3 + 4 * (nt - 2)            # crop + prepare x2, separate TR launches
+    fwi.fwi_plan_destroy(plan)
