@@ -43,7 +43,7 @@ typedef enum fwi_status {
   FWI_EINVAL = 1,       /* bad argument, size or index list                        */
   FWI_ENOMEM = 2,       /* workspace too small / host allocation failed            */
   FWI_EUNSTABLE = 3,    /* c0 outside (0, c_ref]: scheme unstable (App. B)         */
-  FWI_ETIMEOUT = 4,     /* a bounded device wait gave up                           */
+  FWI_ETIMEOUT = 4,     /* reserved: no kernel here waits on a device flag         */
   FWI_ECUDA = 5,        /* a CUDA runtime call failed                              */
   FWI_ECANCELLED = 6,   /* work was cancelled before it ran                        */
   FWI_ENOTSUP = 7       /* grid shape not supported by the library                 */
