@@ -372,7 +372,8 @@ fwi_status fwi_adjoint_source_noalloc(const float *traces, const float *observed
  * output pointers are part of the key: callers that want replays pass the same
  * misfit and grad buffers on every call.  Plans must not be used elsewhere
  * while a batch that contains them runs.  Results are identical to n separate
- * fwi_gradient calls.  Errors: FWI_EINVAL, FWI_ECUDA.
+ * fwi_gradient calls.  Each plan appears once (a plan listed twice, or one
+ * without a bound workspace, is FWI_EINVAL).  Errors: FWI_EINVAL, FWI_ECUDA.
  */
 typedef struct fwi_batch fwi_batch;
 fwi_status fwi_batch_create(int32_t n, fwi_plan *const *plans, fwi_batch **out);

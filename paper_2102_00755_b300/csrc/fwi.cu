@@ -1520,8 +1520,12 @@ struct fwi_batch {
 
 fwi_status fwi_batch_create(int32_t n, fwi_plan* const* plans, fwi_batch** out) {
   if (n < 1 || !plans || !out) return FWI_EINVAL;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!plans[i] || !plans[i]->ws) return FWI_EINVAL;
+    // a plan listed twice would run on two chains at once over one workspace
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return FWI_EINVAL;
+  }
   fwi_batch* b = new (std::nothrow) fwi_batch();
   if (!b) return FWI_ENOMEM;
   b->plans.assign(plans, plans + n);

@@ -117,3 +117,13 @@ def test_batch_recaptures_after_rebinding_and_schedule_change():
     assert torch.equal(Ds[1], D1a) and torch.equal(gs[1], g1a)
     assert all(p.status() == fwi.FWI_OK for p in plans)
     del old
+
+
+def test_batch_refuses_a_plan_listed_twice():
+    """Two chains of one batch would run a plan listed twice over one workspace at once."""
+    fbuild.build()
+    plan = fwi.Plan.from_workload(_instances(8)[0], max_shots=1)
+    st, handle = fwi.fwi_batch_create([plan.handle, plan.handle])
+    assert st == fwi.FWI_EINVAL and not handle
+    with pytest.raises(RuntimeError):
+        fwi.Batch([plan, plan])
