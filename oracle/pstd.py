@@ -24,8 +24,9 @@ Readings where the paper is silent (all listed in the design notes):
   kappa and dt; the Nyquist wavenumber of an even axis is -pi/dx.
 * PML: sigma(d) = alpha (c_ref/dx) (d/P)^4 for distance d (cells) into a layer
   of P cells inside the grid, Lambda = exp(-sigma dt / 2), applied twice per
-  update as Alg. 1 nests it (parity unpinned: the paper only says "multiplication
-  operators"; the tests pin its qualitative properties only).
+  update as Alg. 1 nests it.  The nesting is pinned by the closed form of a uniformly
+  absorbing medium; the profile values are parity unpinned (the paper only says
+  "multiplication operators"; the tests pin their qualitative properties only).
 * pairing="literal" runs Alg. 1 exactly as printed.  pairing="exact" is the
   exact discrete adjoint of the (PML-free) scheme: the adjoint injects the
   cumulative residual Q^j at its step j = 0..Nt and its state after step j is

@@ -119,6 +119,47 @@ def test_homogeneous_closed_form(c):
         assert np.abs(fields[n] - p_exact).max() < 1e-11 * ref, n
 
 
+@pytest.mark.parametrize("c", [1800.0, 1500.0])
+def test_uniform_absorption_closed_form(c):
+    """With the PML multiplier Lambda the same at every voxel and on every axis (a uniformly
+    absorbing medium), Alg. 1's nesting v <- Lambda (Lambda v - dt/rho0 d+ p), rho <-
+    Lambda (Lambda rho - dt rho0 d- v) + source gives, per Fourier mode, the pressure
+    after step n as P_n = lam^(n+1) Q_n with lam = Lambda^2, where Q_n obeys the lossless
+    recurrence of the closed form above driven by s_n / lam^(n+1) instead of s_n: the
+    Lambda factors of the two half-steps cancel in the second difference.  Applying Lambda
+    once instead of twice, or adding the source inside the outer multiplication, breaks it."""
+    G = _grid(10, 12, 9)
+    nt = 40
+    Lam = 0.985
+    for a in range(3):
+        G.lam[a] = np.full_like(G.lam[a], Lam)
+        G.lam_s[a] = np.full_like(G.lam_s[a], Lam)
+    lam = Lam * Lam
+    cc = np.full(G.shape, c)
+    src = np.array([3 + 10 * (4 + 12 * 2)])
+    s = synth.ricker(nt, G.dt, 0.3e6)
+    _, _, fields = pstd.forward(G, cc, src, [1.0], s, np.array([0]), record_field=True)
+    km, _ = _kmag_kappa(G)
+    a = G.c_ref * G.dt * km / 2
+    cos_th = 1.0 - 2.0 * (c / G.c_ref) ** 2 * np.sin(a) ** 2
+    e = np.zeros(G.shape)
+    e.reshape(-1)[src] = 1.0
+    e_hat = np.fft.fftn(e)
+    beta = 2.0 * G.dt / (G.dx * c)
+    sig = np.asarray(s) / lam ** (np.arange(nt) + 1.0)
+    dsig = np.diff(np.concatenate([[0.0], sig]))
+    for n in (0, 1, 5, 17, 39):
+        qh = np.zeros(G.shape, dtype=complex)
+        for m in range(n + 1):
+            qh += c * c * beta * dsig[m] * e_hat * special.eval_chebyu(n - m, cos_th)
+        p_exact = lam ** (n + 1) * np.real(np.fft.ifftn(qh))
+        ref = np.abs(fields[n]).max()
+        assert ref > 0
+        assert np.abs(fields[n] - p_exact).max() < 1e-11 * ref, n
+    # the absorption is visible: the lossless field is larger by lam^-(n+1) at the end
+    assert lam ** nt < 0.31
+
+
 # ---------------------------------------------------------------------------
 # Point-source Green's function (physical scale of the source conversion, App. B)
 # ---------------------------------------------------------------------------
