@@ -128,6 +128,8 @@ fwi_status fwi_plan_bind_workspace(fwi_plan *plan, void *dev_ptr, size_t bytes);
  *   workspace_bytes: out, the plan's new workspace size (the box plan's workspace and
  *                the cropped c0 added, the whole-grid TR simulations removed).
  * Must be called before fwi_plan_bind_workspace; calling it again replaces the box.
+ * The box keeps the default schedule of its own grid: fwi_plan_set_schedule changes the
+ * whole-grid simulations only (the box's launches follow the plan's stream groups).
  * Errors: FWI_EINVAL (bound plan, box outside the grid, Gamma outside the box interior),
  * FWI_ENOTSUP (box size not supported), FWI_ENOMEM.
  */
