@@ -528,6 +528,9 @@ def main():
                     help="gradients timed with the TR re-simulation on a box enclosing Gamma (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=1,
                     help="batched uneven-grid gradients timed beside the headline (single GPU; 0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the short serving stream timed beside the headline (single GPU; 0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=2.0, help="its mean arrival rate (requests/s)")
     ap.add_argument("--nt", type=int, default=0,
                     help="override the number of time samples (small profiling cases only)")
     ap.add_argument("--schedule", default="",
@@ -801,6 +804,44 @@ def main():
         for p in gplans:
             p.close()
 
+    # the serving loop on a short Poisson stream over the 135x135x96 level (1000 steps, forward and
+    # gradient requests, 2..8 encoded emitters): latency percentiles beside throughput, and how many
+    # admitted requests were on the GPU at once
+    served = None
+    if args.serve_requests > 0 and args.workload == "plain" and not args.nt and world == 1:
+        from paper_2102_00755_b300 import serve
+        lv = serve.make_level("L0", synth.serving_level(0, n_src=8, seed=1000), device=dev)
+        server = serve.Server([lv], device=dev, max_inflight=args.inflight)
+        warm = [serve.Request(-1 - i, "L0", kind, np.eye(8)[0], 0.0)
+                for i, kind in enumerate(("forward", "gradient") * 2)]
+        server.run(warm, realtime=False)           # module loading, first calls, graph capture
+        reqs = serve.poisson_stream(["L0"], [1], args.serve_requests, args.serve_rate, 8, seed=3000,
+                                    stratified=True)
+        with ClockSampler(local) as sclk:
+            out = server.run(reqs, realtime=True)
+        sst, res = out["stats"], out["results"]
+        assert all(s_.plan.status() == fwi.FWI_OK for s_ in server.pool["L0"])
+        edges = sorted([(r.admitted, 1) for r in res] + [(r.done, -1) for r in res])
+        cur = peak = 0
+        for _, d in edges:
+            cur += d
+            peak = max(peak, cur)
+        svc = [r.done - r.admitted for r in res]
+        served = {"value": sst["gvoxel_steps_per_s"], "unit": UNIT,
+                  "latency_s": {"p50": sst["p50_s"], "p99": sst["p99_s"]},
+                  "offered_req_per_s": sst["offered_req_per_s"], "achieved_req_per_s": sst["achieved_req_per_s"],
+                  "requests": sst["requests"], "gradients": sst["gradients"], "gradients_per_h": sst["gradients_per_h"],
+                  "in_service_s": {"p50": float(np.percentile(svc, 50)), "p99": float(np.percentile(svc, 99))},
+                  "max_requests_on_gpu": peak, "mean_requests_on_gpu": float(sum(svc) / sst["wall_s"]),
+                  "hbm_frac_at_125B_per_voxel_step": sst["gvoxel_steps_per_s"] * 125.125 / hbm,
+                  "clocks": sclk.summary(),
+                  "form": (f"{args.serve_requests} requests (half gradients, 2..8 encoded emitters) arriving as "
+                           f"a seeded Poisson stream at {args.serve_rate} req/s on the 135x135x96 serving level "
+                           f"(1000 steps, PML), admitted by free HBM up to {args.inflight} at a time, each on its "
+                           f"own stream, pooled plans replaying captured graphs")}
+        server.close()
+        del server, lv
+
     # end to end through the public API with host buffers (pinned), copies inside
     e2e = None
     if args.e2e_steps > 0:
@@ -853,6 +894,7 @@ def main():
         "e2e": e2e,
         "tr_box": trbox,
         "batched": batched,
+        "served": served,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,
