@@ -16,9 +16,20 @@ from scipy import special
 from oracle import pstd
 from paper_2102_00755_b300 import synth
 
-os.environ.setdefault("ORACLE_WORKERS", "1")
-
 C_REF = 1800.0
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _one_fft_worker():
+    """The pins run small grids, where one FFT thread is fastest.  The setting lasts only
+    while this module runs (pytest imports every test module before running any), so the
+    parity tests' large oracle runs keep every core.  A value set by the caller stands."""
+    preset = "ORACLE_WORKERS" in os.environ
+    if not preset:
+        os.environ["ORACLE_WORKERS"] = "1"
+    yield
+    if not preset:
+        os.environ.pop("ORACLE_WORKERS", None)
 
 
 def _grid(nx, ny, nz, dx=1e-3, pml=(0, 0, 0)):
