@@ -185,3 +185,82 @@ def test_launch_count_follows_the_schedule(L):
     fb, gb = launches(stream_groups=1)
     assert fb == f1 and gb - g1 == 3 + 4 * (nt - 2)            # crop + prepare x2, separate TR launches
     fwi.fwi_plan_destroy(plan)
+
+
+def test_plan_create_survives_malformed_problems(L):
+    """Host validation under random problems, valid ones with up to two corruptions (a bad
+    size, count, scalar, enum, an index out of range, an unsorted Gamma, a layer voxel
+    outside Gamma): every answer is a defined status, nothing crashes, and an accepted
+    problem gives a plan whose workspace size, voxel-step and launch counts and TR-box
+    validation can be queried (no GPU needed)."""
+    from hypothesis import HealthCheck, given, settings
+    from hypothesis import strategies as st
+
+    statuses = {fwi.FWI_OK, fwi.FWI_EINVAL, fwi.FWI_ENOMEM, fwi.FWI_ENOTSUP}
+    sizes = st.sampled_from([2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 20])
+    corruptions = ["nx", "nt", "pml", "max_shots", "pairing", "spl", "psm", "dx", "dt", "c_ref",
+                   "src_range", "rec_range", "gamma_order", "layer_outside", "gamma_empty"]
+    seen = {"ok": 0, "box_ok": 0}
+
+    @settings(max_examples=int(os.environ.get("FWI_FUZZ_EXAMPLES", "500")), deadline=None, suppress_health_check=list(HealthCheck))
+    @given(n=st.tuples(sizes, sizes, sizes), nt=st.integers(3, 6), seed=st.integers(0, 2 ** 16),
+           max_shots=st.integers(1, 8), pairing=st.integers(0, 1), spl=st.integers(0, 3), psm=st.integers(0, 1),
+           bad=st.lists(st.sampled_from(corruptions), max_size=2),
+           box=st.tuples(*[st.integers(-1, 12)] * 7), whole=st.booleans())
+    def check(n, nt, seed, max_shots, pairing, spl, psm, bad, box, whole):
+        rng = np.random.default_rng(seed)
+        nx, ny, nz = n
+        nvox = nx * ny * nz
+        pml = [int(rng.integers(0, m // 2 + 1)) for m in n]
+        src = rng.integers(0, nvox, size=int(rng.integers(1, 5))).astype(np.int32)
+        rec = rng.integers(0, nvox, size=int(rng.integers(1, 5))).astype(np.int32)
+        gam = np.unique(rng.integers(0, nvox, size=int(rng.integers(1, 9)))).astype(np.int32)
+        lay = gam[rng.random(len(gam)) < 0.5].copy()
+        dx, dt, c_ref = 1e-3, 1e-7, 1500.0
+        wav = np.ones(nt + 8, np.float32)
+        for b in bad:
+            if b == "nx": nx = int(rng.choice([-1, 0, 1, 7 * 11, 1 << 20]))
+            if b == "nt": nt = int(rng.choice([-1, 0, 2]))
+            if b == "pml": pml[int(rng.integers(0, 3))] = int(rng.choice([-1, 100]))
+            if b == "max_shots": max_shots = int(rng.choice([-1, 0, 64]))
+            if b == "pairing": pairing = int(rng.choice([-1, 2]))
+            if b == "spl": spl = -1
+            if b == "psm": psm = int(rng.choice([-1, 2]))
+            if b == "dx": dx = float(rng.choice([0.0, -1.0, float("nan")]))
+            if b == "dt": dt = float(rng.choice([0.0, -1.0, float("nan")]))
+            if b == "c_ref": c_ref = float(rng.choice([0.0, -1.0, float("nan")]))
+            if b == "src_range": src[0] = int(rng.choice([-1, nvox]))
+            if b == "rec_range": rec[-1] = int(rng.choice([-1, nvox]))
+            if b == "gamma_order" and len(gam) > 1: gam = gam[::-1].copy()
+            if b == "layer_outside": lay = np.append(lay, np.int32(nvox - 1 if nvox - 1 not in gam else -1))
+            if b == "gamma_empty": gam = gam[:0]
+        keep = [np.ascontiguousarray(a, dtype=np.int32) for a in (src, rec, gam, lay)]
+        P = fwi.fwi_problem()
+        P.nx, P.ny, P.nz, P.nt = nx, ny, nz, nt
+        P.pml[0], P.pml[1], P.pml[2] = pml
+        P.dx, P.dt, P.c_ref, P.rho0, P.pml_alpha, P.c_rec = dx, dt, c_ref, 1000.0, 2.0, 0.0
+        P.n_src, P.n_rec, P.n_gamma, P.n_layer = [len(k) for k in keep]
+        ip = ctypes.POINTER(ctypes.c_int32)
+        P.src_idx, P.rec_idx, P.gamma_idx, P.layer_idx = [k.ctypes.data_as(ip) for k in keep]
+        P.wavelet = wav.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        P.pairing, P.max_shots, P.sims_per_launch, P.per_shot_models = pairing, max_shots, spl, psm
+        status, plan, nbytes = fwi.fwi_plan_create(P)
+        assert status in statuses
+        if status != fwi.FWI_OK:
+            return
+        seen["ok"] += 1
+        assert nbytes > 0
+        for K in (1, max_shots):
+            assert fwi.fwi_plan_voxel_steps(plan, K, 1) > 0
+            assert L.fwi_plan_launches(plan, K, 1) > 0
+        if whole:                        # the whole grid as the box, no PML: always valid
+            box = (0, 0, 0, nx, ny, nz, 0)
+        s_box, ws_box = fwi.fwi_plan_set_tr_box(plan, box[0:3], box[3:6], (box[6],) * 3)
+        assert s_box in statuses and (s_box == fwi.FWI_OK or not whole)
+        if s_box == fwi.FWI_OK:
+            seen["box_ok"] += 1
+            assert ws_box > 0 and fwi.fwi_plan_voxel_steps(plan, 1, 1) > 0
+        fwi.fwi_plan_destroy(plan)
+
+    check()
+    assert seen["ok"] > 50 and seen["box_ok"] > 0, seen
